@@ -1,0 +1,150 @@
+"""Pins of the oracle's matching pursuit loops (CPU only).
+
+* plain MP (signal domain) against MP by definition with an explicit
+  dictionary and numpy least squares (Sec. 2.2, real pairs of Sec. 5);
+* coefficient-domain MP with eps = 0 against plain MP: with the full Gram
+  matrix the coefficient-domain residual is exactly D^* r_k (Sec. 3);
+* the energy identity ||r_k||^2 = ||x||^2 - sum of the energy drops;
+* for eps > 0 the bound |<r_k, d_p> - rho_k(p)| <= 2 eps sum_l |c_l| that the
+  proof of Theorem 1 (appendix) gives, doubled for real atom pairs;
+* a signal made of one atom is recovered in one step;
+* the stop rules.
+"""
+import numpy as np
+import pytest
+
+from oracle import cmp, explicit
+from paper_2202_12380_gb300 import inputs
+
+
+def _tiny_dicts():
+    return [(inputs.blackman(16), 4, 16), (inputs.hann(32), 8, 32)]
+
+
+def test_plain_matches_definition_tiny():
+    L = 96
+    dicts = _tiny_dicts()
+    x = np.random.default_rng(5).standard_normal(L)
+    K = 40
+    atoms, energies, r = explicit.mp_definition(dicts, x, K)
+    res = cmp.mp_plain(dicts, x, K, 400.0, fullscan=True)
+    assert res.stop == cmp.STOP_KMAX and res.n_atoms == K
+    for i, (w, m, n, c) in enumerate(atoms):
+        assert (res.dict[i], res.m[i], res.n[i]) == (w, m, n), i
+        assert abs(res.c[i] - c) < 1e-10 * max(1.0, abs(c))
+    # energy bookkeeping of eq. projenfaster equals the true residual energy
+    assert np.max(np.abs(res.E - energies[1:])) < 1e-10 * energies[0]
+    assert np.max(np.abs(res.extra - r)) < 1e-10
+
+
+def test_plain_asymmetric_window_uses_conj_gamma():
+    """With an asymmetric window <d, conj d> is complex; least squares needs
+    conj(gamma) in the numerator of eq. dualatprod (the printed gamma gives a
+    different value), and the definition-based MP decides."""
+    L = 96
+    rng = np.random.default_rng(6)
+    g = rng.uniform(0.2, 1.0, 16)
+    g /= np.linalg.norm(g)
+    dicts = [(g, 4, 16)]
+    x = rng.standard_normal(L)
+    atoms, energies, _ = explicit.mp_definition(dicts, x, 20)
+    res = cmp.mp_plain(dicts, x, 20, 400.0)
+    for i, (w, m, n, c) in enumerate(atoms):
+        assert (res.dict[i], res.m[i], res.n[i]) == (w, m, n)
+        assert abs(res.c[i] - c) < 1e-10
+    assert np.max(np.abs(res.E - energies[1:])) < 1e-10 * energies[0]
+
+
+@pytest.mark.parametrize("case", ["single", "asym", "fig2", "multi3"])
+def test_coef_eps0_equals_plain(case):
+    if case == "single":
+        L, dicts = 2048, [(inputs.gauss_edge(64), 16, 64)]
+    elif case == "asym":
+        # complex <d, conj d>: pins the conj(gamma) of eq. dualatprod and the
+        # gamma read off the own kernel
+        g = np.random.default_rng(7).uniform(0.2, 1.0, 32)
+        L, dicts = 1024, [(g / np.linalg.norm(g), 8, 32), (inputs.blackman(64), 16, 64)]
+    elif case == "fig2":
+        L, dicts = 512, [(inputs.blackman(32), 16, 32), (inputs.hann(8), 4, 8)]
+    else:
+        L, dicts = 2048, [(inputs.blackman(w), w // 4, w) for w in (32, 64, 128)]
+    x = inputs.mixture(L, 11, fs=8000.0)
+    K = 150
+    a = cmp.mp_plain(dicts, x, K, 400.0, fullscan=True)
+    b = cmp.mp_coef(dicts, x, 0.0, K, 400.0, fullscan=True)
+    assert a.n_atoms == b.n_atoms == K
+    assert np.array_equal(a.dict, b.dict) and np.array_equal(a.m, b.m) and np.array_equal(a.n, b.n)
+    assert np.max(np.abs(a.c - b.c) / np.abs(a.c)) < 1e-9
+    assert np.max(np.abs(a.E - b.E)) < 1e-9 * a.E0
+
+
+def test_energy_identity_plain():
+    L = 1024
+    dicts = [(inputs.blackman(w), w // 4, w) for w in (32, 128)]
+    x = inputs.mixture(L, 12, fs=8000.0)
+    res = cmp.mp_plain(dicts, x, 120, 400.0)
+    for k in (1, 10, 60, 120):
+        class S:
+            pass
+        s = S()
+        s.dict, s.m, s.n, s.c = res.dict[:k], res.m[:k], res.n[:k], res.c[:k]
+        r = x - cmp.synth(dicts, s, L)
+        assert abs(float(r @ r) - res.E[k - 1]) < 1e-10 * res.E0
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-3, 1e-2])
+def test_coef_theorem1_bound(eps):
+    """|<r_k, d_p> - rho_k(p)| <= 2 eps sum_l |c_l| for every p (proof of
+    Theorem 1; factor 2 for the two atoms of each real pair)."""
+    L = 2048
+    dicts = [(inputs.blackman(w), w // 4, w) for w in (64, 256)]
+    x = inputs.mixture(L, 13, fs=8000.0)
+    res = cmp.mp_coef(dicts, x, eps, 300, 400.0, planes=True)
+    r = x - cmp.synth(dicts, res, L)
+    bound = 2 * eps * np.sum(np.abs(res.c))
+    worst = 0.0
+    for (g, a, M), rho in zip(dicts, res.extra):
+        true = cmp.dgt(r, g, a, M)
+        worst = max(worst, float(np.max(np.abs(true - rho))))
+    assert worst <= bound
+    assert worst > 0.0  # truncation does change the residual
+
+
+def test_single_atom_recovered():
+    L = 1024
+    dicts = [(inputs.blackman(128), 32, 128), (inputs.blackman(64), 16, 64)]
+    c = 0.7 - 0.4j
+
+    class S:
+        pass
+
+    s = S()
+    s.dict, s.m, s.n, s.c = np.array([0], np.int32), np.array([9], np.int32), \
+        np.array([5], np.int64), np.array([c])
+    x = cmp.synth(dicts, s, L)
+    for res in (cmp.mp_plain(dicts, x, 3, 400.0), cmp.mp_coef(dicts, x, 0.0, 3, 400.0)):
+        assert (res.dict[0], res.m[0], res.n[0]) == (0, 9, 5)
+        assert abs(res.c[0] - c) < 1e-12
+        assert abs(res.E[0]) < 1e-12 * res.E0
+        assert res.stop in (cmp.STOP_NEGENERGY, cmp.STOP_SNR)
+        assert res.n_atoms == 1
+
+
+def test_stop_rules():
+    L = 512
+    dicts = [(inputs.blackman(64), 16, 64)]
+    x = inputs.mixture(L, 14, fs=8000.0)
+    # all-zero input: energy estimate already exhausted
+    z = cmp.mp_coef(dicts, np.zeros(L), 1e-4, 10, 40.0)
+    assert z.n_atoms == 0 and z.stop == cmp.STOP_NEGENERGY
+    # Kmax = 0
+    k0 = cmp.mp_coef(dicts, x, 1e-4, 0, 40.0)
+    assert k0.n_atoms == 0 and k0.stop == cmp.STOP_KMAX
+    # SNR target: stops at the first k with E_k <= E0 10^(-snr/10)
+    r = cmp.mp_coef(dicts, x, 1e-4, 5000, 20.0)
+    assert r.stop == cmp.STOP_SNR
+    thr = r.E0 * 10 ** (-20.0 / 10)
+    assert r.E[-1] <= thr and np.all(r.E[:-1] > thr)
+    # without a target the estimate eventually goes negative (Sec. 6.1 rule)
+    big = cmp.mp_coef(dicts, x, 5e-2, 200000, 400.0)
+    assert big.stop == cmp.STOP_NEGENERGY and big.E[-1] <= 0 and np.all(big.E[:-1] > 0)
