@@ -1,0 +1,488 @@
+// C ABI: state management, analysis, the MP launch, atom read-back and
+// synthesis.  Host code only orchestrates; every arithmetic step of the
+// method runs in the kernels of mp_plan.cu, mp_analysis.cu, mp_loop.cu and
+// mp_synth.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "mp_internal.cuh"
+
+using namespace mpg;
+
+static thread_local char g_err[512] = "";
+
+extern "C" void mpg_set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+extern "C" const char* mp_last_error(void) { return g_err; }
+
+struct mp_state {
+    const mp_plan* plan;
+    int B;
+    std::vector<long long> L;
+    std::vector<DevSig> hs;  // host copy of the static descriptor fields
+    DevSig* d_sigs;
+    int* d_order;
+    void* pool;              // planes, trees, signal copies
+    long long* d_tile_prefix[MAXW];
+    long long total_tiles[MAXW];
+    long long* d_frame_prefix[MAXW];
+    long long total_frames[MAXW];
+    int* d_group_prefix;
+    long long total_groups;
+    int Tmax;
+    size_t smem;
+    long long cap;           // atom capacity per signal
+    mp_atom* d_atoms;
+    double* d_errs;
+    double* d_scalar;
+    double time_limit_s;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e, const char* what) {
+    mpg_set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? MP_ENOMEM : MP_ECUDA;
+}
+
+#define CKR(call)                                                  \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);        \
+    } while (0)
+
+void state_free(mp_state* s) {
+    if (!s) return;
+    if (s->d_sigs) cudaFree(s->d_sigs);
+    if (s->d_order) cudaFree(s->d_order);
+    if (s->pool) cudaFree(s->pool);
+    for (int w = 0; w < MAXW; ++w) {
+        if (s->d_tile_prefix[w]) cudaFree(s->d_tile_prefix[w]);
+        if (s->d_frame_prefix[w]) cudaFree(s->d_frame_prefix[w]);
+    }
+    if (s->d_group_prefix) cudaFree(s->d_group_prefix);
+    if (s->d_atoms) cudaFree(s->d_atoms);
+    if (s->d_errs) cudaFree(s->d_errs);
+    if (s->d_scalar) cudaFree(s->d_scalar);
+    delete s;
+}
+
+int validate_lengths(const mp_plan* p, int B, const int64_t* L) {
+    if (B < 1 || !L) {
+        mpg_set_error("mp_analyze: need B >= 1 and a length array");
+        return MP_EINVAL;
+    }
+    int wmax = 0;
+    for (int w = 0; w < p->W; ++w) wmax = std::max(wmax, p->wlen[w]);
+    for (int b = 0; b < B; ++b) {
+        if (L[b] <= 0) {
+            mpg_set_error("mp_analyze: signal %d has length %lld", b, (long long)L[b]);
+            return MP_EINVAL;
+        }
+        for (int w = 0; w < p->W; ++w)
+            if (L[b] % p->a[w] || L[b] % p->M[w]) {
+                mpg_set_error("mp_analyze: length %lld of signal %d is not a multiple of a=%d "
+                              "and M=%d", (long long)L[b], b, p->a[w], p->M[w]);
+                return MP_EINVAL;
+            }
+        if (L[b] < 2LL * wmax) {
+            mpg_set_error("mp_analyze: length %lld of signal %d is below 2 max(w) = %d",
+                          (long long)L[b], b, 2 * wmax);
+            return MP_EINVAL;
+        }
+        unsigned long long P = 0;
+        for (int w = 0; w < p->W; ++w) P += (unsigned long long)(L[b] / p->a[w]) * (p->M[w] / 2 + 1);
+        if (P >= 0xffffffffull) {
+            mpg_set_error("mp_analyze: signal %d has %llu coefficients (limit 2^32-1)", b, P);
+            return MP_EINVAL;
+        }
+    }
+    return MP_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
+    mp_state* s = new mp_state();
+    memset(s->d_tile_prefix, 0, sizeof(s->d_tile_prefix));
+    memset(s->d_frame_prefix, 0, sizeof(s->d_frame_prefix));
+    s->plan = p;
+    s->B = B;
+    s->L.assign(L, L + B);
+    s->hs.resize(B);
+    s->d_sigs = nullptr;
+    s->d_order = nullptr;
+    s->pool = nullptr;
+    s->d_group_prefix = nullptr;
+    s->d_atoms = nullptr;
+    s->d_errs = nullptr;
+    s->d_scalar = nullptr;
+    s->cap = 0;
+    s->time_limit_s = 0.0;
+    s->Tmax = 1;
+    const int W = p->W;
+    // layout of every signal inside one pool
+    size_t off = 0;
+    std::vector<size_t> o_plane(B * W), o_l0(B * W), o_l1(B * W), o_grp(B), o_x(B);
+    for (int b = 0; b < B; ++b) {
+        DevSig& S = s->hs[b];
+        memset(&S, 0, sizeof(S));
+        S.L = L[b];
+        long long F = 0;
+        unsigned fb = 0;
+        for (int w = 0; w < W; ++w) {
+            const DevDict& D = p->dp.d[w];
+            S.N[w] = L[b] / D.a;
+            S.fbase[w] = fb;
+            fb += (unsigned)(S.N[w] * D.Mr);
+            F += S.N[w];
+            o_plane[b * W + w] = off;
+            off = align256(off + sizeof(float2) * S.N[w] * D.Mrp);
+            o_l0[b * W + w] = off;
+            off = align256(off + sizeof(Entry) * S.N[w] * D.nch);
+            o_l1[b * W + w] = off;
+            off = align256(off + sizeof(Entry) * S.N[w]);
+        }
+        S.fbase[W] = fb;
+        int gs = 0;
+        if (F > TOPCAP) {
+            for (gs = 1; gs < 40; ++gs) {
+                long long T = 0;
+                for (int w = 0; w < W; ++w) T += (S.N[w] + (1LL << gs) - 1) >> gs;
+                if (T <= TOPCAP) break;
+            }
+        }
+        S.gshift = gs;
+        int tb = 0;
+        for (int w = 0; w < W; ++w) {
+            S.tbase[w] = tb;
+            tb += (int)((S.N[w] + (1LL << gs) - 1) >> gs);
+        }
+        S.tbase[W] = tb;
+        S.T = tb;
+        s->Tmax = std::max(s->Tmax, tb);
+        o_grp[b] = off;
+        if (gs > 0) off = align256(off + sizeof(Entry) * tb);
+        o_x[b] = off;
+        off = align256(off + sizeof(float) * L[b]);
+    }
+    cudaError_t e = cudaMalloc(&s->pool, std::max<size_t>(off, 256));
+    if (e != cudaSuccess) {
+        state_free(s);
+        return cuda_fail(e, "mp_analyze: allocating coefficient planes");
+    }
+    char* base = (char*)s->pool;
+    for (int b = 0; b < B; ++b) {
+        DevSig& S = s->hs[b];
+        for (int w = 0; w < W; ++w) {
+            S.plane[w] = (float2*)(base + o_plane[b * W + w]);
+            S.l0[w] = (Entry*)(base + o_l0[b * W + w]);
+            S.l1[w] = (Entry*)(base + o_l1[b * W + w]);
+        }
+        S.grp = S.gshift > 0 ? (Entry*)(base + o_grp[b]) : nullptr;
+        S.x = (const float*)(base + o_x[b]);
+    }
+    // zero the pool once so padding bins are zero
+    cudaStream_t st = p->stream;
+    e = cudaMemsetAsync(s->pool, 0, std::max<size_t>(off, 256), st);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_sigs, sizeof(DevSig) * B);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->d_sigs, s->hs.data(), sizeof(DevSig) * B, cudaMemcpyHostToDevice, st);
+    // CTA order: longest signal first
+    std::vector<int> order(B);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return L[x] > L[y]; });
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_order, sizeof(int) * B);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->d_order, order.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st);
+    // per-dictionary work tables for the analysis and the tree build
+    for (int w = 0; w < W && e == cudaSuccess; ++w) {
+        std::vector<long long> tp(B + 1, 0), fp(B + 1, 0);
+        for (int b = 0; b < B; ++b) {
+            tp[b + 1] = tp[b] + (s->hs[b].N[w] + 63) / 64;
+            fp[b + 1] = fp[b] + s->hs[b].N[w];
+        }
+        s->total_tiles[w] = tp[B];
+        s->total_frames[w] = fp[B];
+        e = cudaMalloc(&s->d_tile_prefix[w], sizeof(long long) * (B + 1));
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_frame_prefix[w], sizeof(long long) * (B + 1));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s->d_tile_prefix[w], tp.data(), sizeof(long long) * (B + 1),
+                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s->d_frame_prefix[w], fp.data(), sizeof(long long) * (B + 1),
+                                cudaMemcpyHostToDevice, st);
+        // host vectors must outlive the async copies
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e == cudaSuccess) {
+        std::vector<int> gp(B + 1, 0);
+        for (int b = 0; b < B; ++b) gp[b + 1] = gp[b] + (s->hs[b].gshift > 0 ? s->hs[b].T : 0);
+        s->total_groups = gp[B];
+        e = cudaMalloc(&s->d_group_prefix, sizeof(int) * (B + 1));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s->d_group_prefix, gp.data(), sizeof(int) * (B + 1),
+                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_scalar, sizeof(double) * 4);
+    if (e != cudaSuccess) {
+        state_free(s);
+        return cuda_fail(e, "mp_analyze: state set-up");
+    }
+    s->smem = mp_loop_smem_bytes(s->Tmax, W);
+    *out = s;
+    return MP_OK;
+}
+
+int analyze_impl(const mp_plan* p, mp_state** state, int B, const float* const* x,
+                 const int64_t* L, cudaMemcpyKind kind) {
+    if (!p || !state || !x) {
+        mpg_set_error("mp_analyze: null argument");
+        return MP_EINVAL;
+    }
+    int rc = validate_lengths(p, B, L);
+    if (rc) return rc;
+    for (int b = 0; b < B; ++b)
+        if (!x[b]) {
+            mpg_set_error("mp_analyze: signal pointer %d is null", b);
+            return MP_EINVAL;
+        }
+    mp_state* s = *state;
+    if (s) {
+        bool same = s->plan == p && s->B == B;
+        for (int b = 0; same && b < B; ++b) same = s->L[b] == L[b];
+        if (!same) {
+            mpg_set_error("mp_analyze: state was made for another plan or other lengths");
+            return MP_EINVAL;
+        }
+    } else {
+        rc = state_create(p, B, L, &s);
+        if (rc) return rc;
+    }
+    cudaStream_t st = p->stream;
+    for (int b = 0; b < B; ++b)
+        CKR(cudaMemcpyAsync((void*)s->hs[b].x, x[b], sizeof(float) * L[b], kind, st));
+    CKR(launch_energy(s->d_sigs, B, nullptr, 0, st));
+    for (int w = 0; w < p->W; ++w) {
+        const DevDict& D = p->dp.d[w];
+        CKR(launch_analysis_sgemm(p->d_A[w], p->Arows[w], p->Akp[w], D.wlen, D.a, D.Mrp, B,
+                                  s->d_tile_prefix[w], s->d_sigs, w, s->total_tiles[w], st));
+        CKR(launch_tree_build(p->dp, s->d_sigs, B, s->d_frame_prefix[w], s->total_frames[w], w, st));
+    }
+    CKR(launch_group_build(s->d_sigs, B, s->d_group_prefix, s->total_groups, p->W, st));
+    if (kind == cudaMemcpyHostToDevice) CKR(cudaStreamSynchronize(st));
+    *state = s;
+    return MP_OK;
+}
+
+int ensure_capacity(mp_state* s, long long kmax) {
+    if (kmax <= s->cap) return MP_OK;
+    const int B = s->B;
+    cudaStream_t st = s->plan->stream;
+    long long ncap = std::max(kmax, s->cap * 2);
+    mp_atom* na = nullptr;
+    double* ne = nullptr;
+    CKR(cudaMalloc(&na, sizeof(mp_atom) * ncap * B));
+    cudaError_t e = cudaMalloc(&ne, sizeof(double) * ncap * B);
+    if (e != cudaSuccess) {
+        cudaFree(na);
+        return cuda_fail(e, "mp_run: atom buffer");
+    }
+    if (s->cap > 0) {
+        CKR(cudaMemcpy2DAsync(na, sizeof(mp_atom) * ncap, s->d_atoms, sizeof(mp_atom) * s->cap,
+                              sizeof(mp_atom) * s->cap, B, cudaMemcpyDeviceToDevice, st));
+        CKR(cudaMemcpy2DAsync(ne, sizeof(double) * ncap, s->d_errs, sizeof(double) * s->cap,
+                              sizeof(double) * s->cap, B, cudaMemcpyDeviceToDevice, st));
+    }
+    CKR(cudaStreamSynchronize(st));
+    if (s->d_atoms) cudaFree(s->d_atoms);
+    if (s->d_errs) cudaFree(s->d_errs);
+    s->d_atoms = na;
+    s->d_errs = ne;
+    s->cap = ncap;
+    for (int b = 0; b < B; ++b) {
+        s->hs[b].atoms = na + (long long)b * ncap;
+        s->hs[b].errs = ne + (long long)b * ncap;
+        s->hs[b].cap = ncap;
+        // patch only the pointer fields; the dynamic fields live on the device
+        char* dst = (char*)(s->d_sigs + b);
+        CKR(cudaMemcpyAsync(dst + offsetof(DevSig, atoms), &s->hs[b].atoms,
+                            offsetof(DevSig, x) - offsetof(DevSig, atoms), cudaMemcpyHostToDevice,
+                            st));
+    }
+    CKR(cudaStreamSynchronize(st));
+    return MP_OK;
+}
+
+int read_status(mp_state* s, int64_t* n_atoms, int* stop, double* snr, bool* timed_out) {
+    std::vector<DevSig> dv(s->B);
+    CKR(cudaMemcpyAsync(dv.data(), s->d_sigs, sizeof(DevSig) * s->B, cudaMemcpyDeviceToHost,
+                        s->plan->stream));
+    CKR(cudaStreamSynchronize(s->plan->stream));
+    bool to = false;
+    for (int b = 0; b < s->B; ++b) {
+        if (n_atoms) n_atoms[b] = dv[b].k;
+        if (stop) stop[b] = dv[b].stop;
+        if (snr) snr[b] = 10.0 * std::log10(dv[b].E0 / dv[b].E);
+        to = to || dv[b].timed_out;
+    }
+    if (timed_out) *timed_out = to;
+    return MP_OK;
+}
+
+}  // namespace
+
+extern "C" int mp_analyze(const mp_plan* plan, mp_state** state, int B, const float* const* x_dev,
+                          const int64_t* L) {
+    return analyze_impl(plan, state, B, x_dev, L, cudaMemcpyDeviceToDevice);
+}
+
+extern "C" int mp_analyze_host(const mp_plan* plan, mp_state** state, int B,
+                               const float* const* x_host, const int64_t* L) {
+    return analyze_impl(plan, state, B, x_host, L, cudaMemcpyHostToDevice);
+}
+
+extern "C" int mp_state_coefficients(const mp_state* s, int sig, int w, float* host, int64_t cap) {
+    if (!s || sig < 0 || sig >= s->B || w < 0 || w >= s->plan->W || !host) {
+        mpg_set_error("mp_state_coefficients: bad argument");
+        return MP_EINVAL;
+    }
+    const DevDict& D = s->plan->dp.d[w];
+    const long long N = s->hs[sig].N[w];
+    if (cap < 2 * N * D.Mr) {
+        mpg_set_error("mp_state_coefficients: buffer too small");
+        return MP_EINVAL;
+    }
+    CKR(cudaMemcpy2DAsync(host, sizeof(float2) * D.Mr, s->hs[sig].plane[w], sizeof(float2) * D.Mrp,
+                          sizeof(float2) * D.Mr, N, cudaMemcpyDeviceToHost, s->plan->stream));
+    CKR(cudaStreamSynchronize(s->plan->stream));
+    return MP_OK;
+}
+
+extern "C" int mp_state_set_time_limit(mp_state* s, double seconds) {
+    if (!s || !std::isfinite(seconds)) {
+        mpg_set_error("mp_state_set_time_limit: bad argument");
+        return MP_EINVAL;
+    }
+    s->time_limit_s = seconds;
+    return MP_OK;
+}
+
+extern "C" int mp_run_async(mp_state* s, int64_t K_max, double target_snr_db) {
+    if (!s || K_max < 0 || std::isnan(target_snr_db)) {
+        mpg_set_error("mp_run: bad argument");
+        return MP_EINVAL;
+    }
+    int rc = ensure_capacity(s, std::max<long long>(K_max, 1));
+    if (rc) return rc;
+    const double thr_scale = std::pow(10.0, -target_snr_db / 10.0);
+    const long long budget =
+        s->time_limit_s > 0 ? (long long)std::min(s->time_limit_s * 1e9, 9e18) : 0LL;
+    CKR(launch_mp_loop(s->plan->dp, s->d_sigs, s->d_order, s->B, K_max, thr_scale, budget, s->smem,
+                       s->plan->stream));
+    return MP_OK;
+}
+
+extern "C" int mp_get_status(mp_state* s, int64_t* n_atoms, int* stop, double* snr) {
+    if (!s) {
+        mpg_set_error("mp_get_status: null state");
+        return MP_EINVAL;
+    }
+    bool to = false;
+    int rc = read_status(s, n_atoms, stop, snr, &to);
+    if (rc) return rc;
+    if (to) {
+        mpg_set_error("mp_run: time limit reached before every signal stopped");
+        return MP_ETIMEOUT;
+    }
+    return MP_OK;
+}
+
+extern "C" int mp_run(mp_state* s, int64_t K_max, double target_snr_db, int64_t* n_atoms,
+                      int* stop_reason, double* final_snr_db) {
+    int rc = mp_run_async(s, K_max, target_snr_db);
+    if (rc) return rc;
+    return mp_get_status(s, n_atoms, stop_reason, final_snr_db);
+}
+
+extern "C" int mp_get_atoms(const mp_state* s, int sig, mp_atom* out, int64_t cap, int64_t* n) {
+    if (!s || sig < 0 || sig >= s->B) {
+        mpg_set_error("mp_get_atoms: bad argument");
+        return MP_EINVAL;
+    }
+    long long k = 0;
+    CKR(cudaMemcpyAsync(&k, (const char*)(s->d_sigs + sig) + offsetof(DevSig, k), sizeof(k),
+                        cudaMemcpyDeviceToHost, s->plan->stream));
+    CKR(cudaStreamSynchronize(s->plan->stream));
+    if (n) *n = k;
+    long long c = std::min<long long>(k, cap);
+    if (c > 0 && out) {
+        CKR(cudaMemcpyAsync(out, s->hs[sig].atoms, sizeof(mp_atom) * c, cudaMemcpyDeviceToHost,
+                            s->plan->stream));
+        CKR(cudaStreamSynchronize(s->plan->stream));
+    }
+    return MP_OK;
+}
+
+extern "C" int mp_get_errors(const mp_state* s, int sig, double* E, int64_t cap, int64_t* n) {
+    if (!s || sig < 0 || sig >= s->B) {
+        mpg_set_error("mp_get_errors: bad argument");
+        return MP_EINVAL;
+    }
+    long long k = 0;
+    CKR(cudaMemcpyAsync(&k, (const char*)(s->d_sigs + sig) + offsetof(DevSig, k), sizeof(k),
+                        cudaMemcpyDeviceToHost, s->plan->stream));
+    CKR(cudaStreamSynchronize(s->plan->stream));
+    if (n) *n = k;
+    long long c = std::min<long long>(k, cap);
+    if (c > 0 && E) {
+        CKR(cudaMemcpyAsync(E, s->hs[sig].errs, sizeof(double) * c, cudaMemcpyDeviceToHost,
+                            s->plan->stream));
+        CKR(cudaStreamSynchronize(s->plan->stream));
+    }
+    return MP_OK;
+}
+
+extern "C" int mp_synthesize(const mp_state* s, int sig, float* y, double* true_snr_db) {
+    if (!s || sig < 0 || sig >= s->B || !y) {
+        mpg_set_error("mp_synthesize: bad argument");
+        return MP_EINVAL;
+    }
+    cudaStream_t st = s->plan->stream;
+    if (s->cap == 0) {
+        // no MP run yet: the approximation is zero
+        CKR(cudaMemsetAsync(y, 0, sizeof(float) * s->L[sig], st));
+    } else {
+        CKR(launch_synth(s->plan->dp, s->d_sigs + sig, 0, y, s->L[sig], st));
+    }
+    if (true_snr_db) {
+        CKR(launch_resid_energy(s->d_sigs + sig, y, s->L[sig], s->d_scalar, 1, st));
+        double r = 0.0, e0 = 0.0;
+        CKR(cudaMemcpyAsync(&r, s->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CKR(cudaMemcpyAsync(&e0, (const char*)(s->d_sigs + sig) + offsetof(DevSig, E0),
+                            sizeof(double), cudaMemcpyDeviceToHost, st));
+        CKR(cudaStreamSynchronize(st));
+        *true_snr_db = 10.0 * std::log10(e0 / r);
+    }
+    return MP_OK;
+}
+
+extern "C" void mp_state_destroy(mp_state* s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->plan->stream);
+    state_free(s);
+}

@@ -1,0 +1,144 @@
+// Internal data layout shared by the CUDA translation units of libmpgabor.
+//
+// Device memory layout (per signal, per dictionary w):
+//   plane[w]  residual coefficients rho_w(m, n), float2, frame-major
+//             [N_w][Mrp_w] with Mrp_w = 32 * ceil((M_w/2 + 1) / 32); bins
+//             m >= M_w/2 + 1 are zero padding and never selected
+//   l0[w]     max-tree level 0: one Entry per (frame, 32-bin chunk)
+//   l1[w]     max-tree level 1: one Entry per frame
+//   grp       level 2 (only when frames do not fit the on-chip top level):
+//             one Entry per group of 2^gshift consecutive frames of one
+//             dictionary
+// An Entry packs the selection key and the coefficient it belongs to:
+//   key = (float bits of |rho|^2) << 32 | (0xffffffff - flat index),
+//   flat = fbase[w] + n * (M_w/2 + 1) + m,
+// so an unsigned max over keys is the argmax of |rho|^2 with ties broken
+// towards the lowest (w, n, m).  |rho|^2 >= 0, so its float bits order like
+// the values.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mpgabor.h"
+
+namespace mpg {
+
+constexpr int MAXW = 8;          // dictionaries per plan
+constexpr int CHUNK = 32;        // bins per level-0 entry (one warp)
+constexpr int TOPCAP = 4096;     // top-level entries held in shared memory
+constexpr int LOOP_THREADS = 512;
+
+struct __align__(16) Entry {
+    unsigned long long key;
+    float2 val;
+};
+
+struct DevDict {
+    int wlen, a, M, Mr, nch, Mrp;  // Mr = M/2+1 stored bins, Mrp padded to CHUNK
+    int gam_lo, gam_hi, gam_off;   // compact <d, conj d> table (see mp_plan.cu)
+    int g_off;                     // offset of the FP32 window in DevPlan::g32
+};
+
+struct DevPair {
+    int rf, rt;      // alignment classes in frequency / time
+    int cls_base;    // first class descriptor of the pair
+    int pad;
+};
+
+// Dense tile of one alignment class: T[c * R + i] = h_eps(delta, tau) with
+// delta = (i_lo + i) rf - cf and tau = (c_lo + c) a_v - ct a_u.
+struct DevClass {
+    long long off;   // float2 offset in the tile pool
+    int R, C, i_lo, c_lo;
+};
+
+struct DevPlan {
+    int W;
+    int pad;
+    DevDict d[MAXW];
+    DevPair p[MAXW * MAXW];
+    const DevClass* cls;
+    const float2* tiles;
+    const float2* gam;
+    const float* g32;
+};
+
+struct DevSig {
+    long long L;
+    long long N[MAXW];
+    unsigned fbase[MAXW + 1];
+    int tbase[MAXW + 1];
+    float2* plane[MAXW];
+    Entry* l0[MAXW];
+    Entry* l1[MAXW];
+    Entry* grp;
+    int gshift;      // log2 of frames per top-level entry
+    int T;           // top-level entries
+    mp_atom* atoms;
+    double* errs;
+    long long cap;
+    const float* x;  // device copy of the signal
+    // dynamic state, written back by the MP launch
+    long long k;
+    double E;
+    double E0;
+    int stop;
+    int timed_out;
+};
+
+// ---- host launchers implemented in the .cu files -------------------------
+// analysis: rho = A * frames for dictionary w of the listed signals
+cudaError_t launch_analysis_sgemm(const float* A, int Arows, int Kp, int w_len, int a, int Mrp,
+                                  int nsig, const long long* d_tile_prefix, const DevSig* d_sigs,
+                                  int dict, long long total_frame_tiles, cudaStream_t st);
+cudaError_t launch_energy(const DevSig* d_sigs, int nsig, double* d_partials, int nparts,
+                          cudaStream_t st);
+cudaError_t launch_tree_build(const DevPlan& P, const DevSig* d_sigs, int nsig,
+                              const long long* d_frame_prefix, long long total_frames, int dict,
+                              cudaStream_t st);
+cudaError_t launch_group_build(const DevSig* d_sigs, int nsig, const int* d_group_prefix,
+                               long long total_groups, int W, cudaStream_t st);
+cudaError_t launch_mp_loop(const DevPlan& P, DevSig* d_sigs, const int* d_order, int nsig,
+                           long long kmax, double thr_scale, long long budget_ns, size_t smem,
+                           cudaStream_t st);
+cudaError_t launch_synth(const DevPlan& P, const DevSig* d_sig, long long natoms, float* y,
+                         long long L, cudaStream_t st);
+cudaError_t launch_resid_energy(const DevSig* d_sig, const float* y, long long L,
+                                double* d_partials, int nparts, cudaStream_t st);
+
+size_t mp_loop_smem_bytes(int T, int W);
+
+}  // namespace mpg
+
+// error helpers (mp_api.cu)
+extern "C" void mpg_set_error(const char* fmt, ...);
+
+#ifdef __cplusplus
+#include <vector>
+
+// host side of an mp_plan (opaque in the C ABI)
+struct mp_plan {
+    int W;
+    int wlen[mpg::MAXW], a[mpg::MAXW], M[mpg::MAXW];
+    double eps;
+    unsigned flags;
+    cudaStream_t stream;
+    int device;
+    mpg::DevPlan dp;  // device view (pointers below)
+    // geometry of every ordered pair (u, v), index u * W + v
+    int Mx[mpg::MAXW * mpg::MAXW], an[mpg::MAXW * mpg::MAXW];
+    int tmin[mpg::MAXW * mpg::MAXW], ntau[mpg::MAXW * mpg::MAXW];
+    double2* d_kern[mpg::MAXW * mpg::MAXW];  // untruncated FP64 kernels [ntau][Mx]
+    std::vector<mpg::DevClass> cls;
+    std::vector<int> cls_nnz;
+    std::vector<float> gam_full[mpg::MAXW];  // <d, conj d>, (M/2+1) complex
+    mpg::DevClass* d_cls;
+    float2* d_tiles;
+    long long tiles_len;
+    float2* d_gam;
+    float* d_g32;
+    float* d_A[mpg::MAXW];  // FP32 DFT matrices for the analysis, [Arows][Akp]
+    int Arows[mpg::MAXW], Akp[mpg::MAXW];
+};
+#endif

@@ -1,0 +1,281 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Plan (cross-kernels, class tiles, <d, conj d>), analysis planes, and full
+decompositions on small workloads that span several tiles and ragged tails,
+plus the 16 kHz single-Gaussian-dictionary workload at full size (L=16384,
+K=500), the Fig. 2 two-dictionary layout, eps = 0 against plain MP, batches
+of uneven lengths and the stop rules.
+"""
+import numpy as np
+import pytest
+
+from oracle import cmp
+from paper_2202_12380_gb300 import inputs
+from tests.parity import compare, first_near_tie
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts too
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2202_12380_gb300 import mpgabor as mg  # noqa: E402
+
+
+def _plan(dicts, eps, flags=0):
+    wins = [g for g, _, _ in dicts]
+    return mg.mp_plan_create(wins, [a for _, a, _ in dicts], [M for _, _, M in dicts], eps, flags)
+
+
+def _run_gpu(dicts, xs, eps, K, snr):
+    plan = _plan(dicts, eps)
+    st = mg.mp_analyze(plan, [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in xs])
+    n, stop, q = mg.mp_run(st, K, snr)
+    out = []
+    for b in range(len(xs)):
+        atoms = mg.mp_get_atoms(st, b)
+        errs = mg.mp_get_errors(st, b)
+        E0 = errs[-1] * 10 ** (q[b] / 10) if errs.size else float(np.sum(xs[b].astype(np.float64) ** 2))
+        out.append((atoms, errs, E0, int(stop[b])))
+    return plan, st, out
+
+
+def _workload_small(kind):
+    if kind == "single":
+        return 8192, [(inputs.gauss_edge(256), 64, 256)]
+    if kind == "multi3":
+        return 16384, [(inputs.blackman(w), w // 4, w) for w in (128, 256, 512)]
+    if kind == "fig2":
+        # Fig. 2 layout: a1 = 4 a_min, M1 = 8 a_min; a2 = a_min, M2 = 2 a_min
+        return 4096, [(inputs.blackman(128), 64, 128), (inputs.hann(32), 16, 32)]
+    if kind == "mixed":
+        return 12288, [(inputs.blackman(256), 64, 256), (inputs.gauss_edge(128), 32, 128),
+                       (inputs.hann(512), 128, 512)]
+    raise KeyError(kind)
+
+
+# ---------------------------------------------------------------- plan -----
+
+@pytest.mark.parametrize("kind", ["multi3", "fig2", "mixed"])
+def test_kernels_fp64_match_oracle(kind):
+    L, dicts = _workload_small(kind)
+    plan = _plan(dicts, 1e-4)
+    for u in range(len(dicts)):
+        for v in range(len(dicts)):
+            h_gpu, taus = mg.mp_plan_kernel_fp64(plan, u, v)
+            h_ref, taus_ref, Mx, an = cmp.kernel(dicts[u], dicts[v])
+            assert np.array_equal(taus, taus_ref)
+            assert np.max(np.abs(h_gpu - h_ref)) < 1e-13
+
+
+@pytest.mark.parametrize("kind", ["multi3", "fig2", "mixed"])
+@pytest.mark.parametrize("eps", [1e-4, 1e-2])
+def test_class_tiles_cover_truncated_kernel(kind, eps):
+    """Every entry |h| > eps lands in exactly one class tile at the position
+    the tile geometry states, rounded to FP32; nothing else is nonzero."""
+    L, dicts = _workload_small(kind)
+    plan = _plan(dicts, eps)
+    for u, (gu, au, Mu) in enumerate(dicts):
+        for v, (gv, av, Mv) in enumerate(dicts):
+            h, taus, Mx, an = cmp.kernel(dicts[u], dicts[v])
+            info0 = mg.mp_plan_tile_info(plan, u, v, 0, 0)
+            rf, rt = info0["rf"], info0["rt"]
+            covered = 0
+            for cf in range(rf):
+                for ct in range(rt):
+                    tile, info = mg.mp_plan_tile(plan, u, v, cf, ct)
+                    R, C, i_lo, c_lo = info["R"], info["C"], info["i_lo"], info["c_lo"]
+                    for c in range(C):
+                        tau = (c_lo + c) * av - ct * au
+                        for i in range(R):
+                            d = ((i_lo + i) * rf - cf) % Mx
+                            it = (tau - taus[0]) // an
+                            ok = 0 <= it < len(taus) and (tau - taus[0]) % an == 0
+                            ref = h[it, d] if ok else 0.0
+                            ref = ref if abs(ref) > eps else 0.0
+                            assert abs(tile[c, i] - np.complex64(ref)) <= 1e-7 * max(1.0, abs(ref))
+                            covered += abs(ref) > 0
+                    assert info["nnz"] == int(np.count_nonzero(np.abs(tile) > 0)) or eps == 0
+            # all significant entries that a (k, j) pair can reach are in some tile
+            reach = 0
+            for it, tau in enumerate(taus):
+                for d in range(Mx):
+                    if abs(h[it, d]) > eps:
+                        reach += 1
+            assert covered == reach
+
+
+def test_gamma_matches_oracle_kernel():
+    L, dicts = _workload_small("mixed")
+    plan = _plan(dicts, 1e-4)
+    for u, (g, a, M) in enumerate(dicts):
+        h, taus, Mx, an = cmp.kernel(dicts[u], dicts[u])
+        it0 = int(np.where(taus == 0)[0][0])
+        gam = mg.mp_plan_gamma(plan, u)
+        for k in range(M // 2 + 1):
+            ref = 0.0 if k in (0, M // 2) else h[it0, (M - 2 * k) % M]
+            ref = ref if abs(ref) > 1e-4 else 0.0
+            assert abs(gam[k] - np.complex64(ref)) <= 1e-7
+
+
+# ------------------------------------------------------------ analysis -----
+
+@pytest.mark.parametrize("kind", ["single", "multi3", "fig2", "mixed"])
+def test_analysis_planes_match_oracle(kind):
+    L, dicts = _workload_small(kind)
+    x = inputs.as_f32(inputs.mixture(L, 21, fs=16000.0))
+    plan = _plan(dicts, 1e-4)
+    st = mg.mp_analyze(plan, [torch.from_numpy(x).cuda()])
+    for w, (g, a, M) in enumerate(dicts):
+        ref = cmp.dgt(x.astype(np.float64), g, a, M)
+        got = mg.mp_state_coefficients(st, 0, w)
+        scale = np.sqrt(np.mean(np.abs(ref) ** 2))
+        err = np.max(np.abs(got - ref)) / scale
+        assert err < 1e-5, err
+
+
+# -------------------------------------------------------- decompositions ---
+
+@pytest.mark.parametrize("kind", ["single", "multi3", "fig2", "mixed"])
+def test_mp_parity_small(kind):
+    L, dicts = _workload_small(kind)
+    x = inputs.as_f32(inputs.mixture(L, 31, fs=16000.0))
+    K = 400
+    ref = cmp.mp_coef(dicts, x.astype(np.float64), 1e-4, K, 200.0)
+    _, _, out = _run_gpu(dicts, [x], 1e-4, K, 200.0)
+    atoms, errs, E0, stop = out[0]
+    assert stop == mg.MP_STOP_KMAX and atoms.size == K
+    r = compare(atoms, errs, E0, ref, min_checked=100)
+    print(kind, r)
+
+
+def test_mp_parity_single_gauss_16k_full():
+    """16 kHz tones + clicks + noise, Gaussian w=256, a=64, M=256, eps=1e-4,
+    K=500, full size (L=16384)."""
+    cfg = inputs.WORKLOADS["single_gauss_16k"]
+    x = inputs.workload_signal("single_gauss_16k")
+    dicts = [(inputs.make_window(k, w), a, M) for (k, w, a, M) in cfg["dicts"]]
+    ref = cmp.mp_coef(dicts, x.astype(np.float64), cfg["eps"], cfg["kmax"], cfg["snr_db"])
+    _, _, out = _run_gpu(dicts, [x], cfg["eps"], cfg["kmax"], cfg["snr_db"])
+    atoms, errs, E0, stop = out[0]
+    assert atoms.size == ref.n_atoms == cfg["kmax"]
+    r = compare(atoms, errs, E0, ref, min_checked=200)
+    print(r)
+
+
+def test_eps0_gpu_matches_plain_mp():
+    """With eps = 0 the truncated Gram matrix is the full one and the GPU
+    decomposition follows plain signal-domain MP."""
+    L, dicts = 2048, [(inputs.blackman(64), 16, 64), (inputs.blackman(128), 32, 128)]
+    x = inputs.as_f32(inputs.mixture(L, 41, fs=8000.0))
+    ref = cmp.mp_plain(dicts, x.astype(np.float64), 150, 200.0)
+    _, _, out = _run_gpu(dicts, [x], 0.0, 150, 200.0)
+    atoms, errs, E0, stop = out[0]
+    compare(atoms, errs, E0, ref, min_checked=50)
+
+
+def test_batched_uneven_lengths():
+    """Several signals of different lengths in one launch, each matching its
+    own oracle run; per-signal stopping by SNR."""
+    dicts = [(inputs.blackman(w), w // 4, w) for w in (128, 256, 512)]
+    lens = [2048, 8192, 4096, 16384, 1024 * 3]
+    xs = [inputs.as_f32(inputs.mixture(L, 50 + i, fs=16000.0, snr_db=15.0 + 3 * i))
+          for i, L in enumerate(lens)]
+    K, snr = 300, 18.0
+    _, _, out = _run_gpu(dicts, xs, 1e-4, K, snr)
+    for x, (atoms, errs, E0, stop) in zip(xs, out):
+        ref = cmp.mp_coef(dicts, x.astype(np.float64), 1e-4, K, snr)
+        compare(atoms, errs, E0, ref, min_checked=20)
+        if first_near_tie(ref) >= ref.n_atoms:
+            assert atoms.size == ref.n_atoms and stop == ref.stop
+
+
+def test_stop_rules_gpu():
+    dicts = [(inputs.blackman(128), 32, 128)]
+    L = 4096
+    x = inputs.as_f32(inputs.mixture(L, 61, fs=16000.0))
+    plan = _plan(dicts, 1e-4)
+    z = np.zeros(L, np.float32)
+    st = mg.mp_analyze(plan, [torch.from_numpy(z).cuda()])
+    n, stop, q = mg.mp_run(st, 10, 40.0)
+    assert n[0] == 0 and stop[0] == mg.MP_STOP_NEGENERGY
+    st2 = mg.mp_analyze(plan, [torch.from_numpy(x).cuda()])
+    n, stop, q = mg.mp_run(st2, 0, 40.0)
+    assert n[0] == 0 and stop[0] == mg.MP_STOP_KMAX
+    bad = x.copy()
+    bad[7] = np.nan
+    st3 = mg.mp_analyze(plan, [torch.from_numpy(bad).cuda()])
+    n, stop, q = mg.mp_run(st3, 10, 40.0)
+    assert n[0] == 0 and stop[0] == mg.MP_STOP_INVALID
+    ref = cmp.mp_coef(dicts, x.astype(np.float64), 5e-2, 100000, 400.0)
+    assert ref.stop == cmp.STOP_NEGENERGY
+    plan2 = _plan(dicts, 5e-2)
+    st4 = mg.mp_analyze(plan2, [torch.from_numpy(x).cuda()])
+    n, stop, q = mg.mp_run(st4, 100000, 400.0)
+    assert stop[0] == mg.MP_STOP_NEGENERGY
+    errs = mg.mp_get_errors(st4, 0)
+    assert errs[-1] <= 0 and np.all(errs[:-1] > 0)
+
+
+def test_resume_and_time_limit():
+    """A run cut by the time limit (MP_ETIMEOUT) leaves a valid state; calling
+    again continues to exactly the uninterrupted result."""
+    L, dicts = _workload_small("multi3")
+    x = inputs.as_f32(inputs.mixture(L, 71, fs=16000.0))
+    K = 600
+    plan = _plan(dicts, 1e-4)
+    st = mg.mp_analyze(plan, [torch.from_numpy(x).cuda()])
+    n_full, _, _ = mg.mp_run(st, K, 200.0)
+    full = mg.mp_get_atoms(st, 0)
+    st2 = mg.mp_analyze(plan, [torch.from_numpy(x).cuda()])
+    mg.mp_state_set_time_limit(st2, 2e-5)
+    calls = 0
+    while True:
+        n, stop, q, to = mg.mp_run(st2, K, 200.0, allow_timeout=True)
+        calls += 1
+        if not to:
+            break
+        assert calls < 100000
+    assert calls > 1
+    part = mg.mp_get_atoms(st2, 0)
+    assert np.array_equal(part, full)
+    # a second mp_run with a larger K_max continues the same decomposition
+    st3 = mg.mp_analyze(plan, [torch.from_numpy(x).cuda()])
+    mg.mp_run(st3, K // 2, 200.0)
+    mg.mp_run(st3, K, 200.0)
+    assert np.array_equal(mg.mp_get_atoms(st3, 0), full)
+
+
+def test_synthesis_matches_oracle():
+    L, dicts = _workload_small("mixed")
+    x = inputs.as_f32(inputs.mixture(L, 81, fs=16000.0))
+    plan = _plan(dicts, 1e-4)
+    st = mg.mp_analyze(plan, [torch.from_numpy(x).cuda()])
+    mg.mp_run(st, 300, 200.0)
+    atoms = mg.mp_get_atoms(st, 0)
+    y = torch.zeros(L, device="cuda")
+    snr = mg.mp_synthesize(st, 0, y)
+
+    class A:
+        pass
+
+    a = A()
+    a.dict, a.m, a.n = atoms["dict"], atoms["m"], atoms["n"]
+    a.c = atoms["re"].astype(np.float64) + 1j * atoms["im"].astype(np.float64)
+    ref = cmp.synth(dicts, a, L)
+    got = y.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - ref)) < 1e-5 * np.max(np.abs(ref))
+    r = x.astype(np.float64) - ref
+    ref_snr = 10 * np.log10(np.sum(x.astype(np.float64) ** 2) / np.sum(r * r))
+    assert abs(snr - ref_snr) < 1e-3
+
+
+def test_analyze_host_matches_device():
+    L, dicts = _workload_small("multi3")
+    x = inputs.as_f32(inputs.mixture(L, 91, fs=16000.0))
+    plan = _plan(dicts, 1e-4)
+    st = mg.mp_analyze(plan, [torch.from_numpy(x).cuda()])
+    mg.mp_run(st, 200, 200.0)
+    st_h = mg.mp_analyze_host(plan, [x])
+    mg.mp_run(st_h, 200, 200.0)
+    assert np.array_equal(mg.mp_get_atoms(st, 0), mg.mp_get_atoms(st_h, 0))
