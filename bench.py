@@ -1,0 +1,475 @@
+"""Benchmark: matching-pursuit atoms/s on GB300 through the C ABI.
+
+One step = one pass of the whole hot path on one batch of synthetic input:
+mp_analyze (multi-Gabor DGT analysis, E_0, max trees) + mp_run (persistent
+selection / update loop until 40 dB residual SNR or K_max atoms).
+
+Default workload (one GPU): ``multi3_2p18`` -- one real signal, L = 2^18 at
+44.1 kHz (chirps, notes, transients, pink noise at 30 dB), three Blackman
+dictionaries w = M = 512/1024/2048 with a = w/4, kernel threshold 1e-4, stop
+at 40 dB or K = 50000 atoms.  The batched form (``batch256``: 256 signals of
+log-uniform length 2^14..2^20, stop at 30 dB or K = 20000) is measured as a
+secondary figure in the same run.
+
+Printed: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2202_12380_gb300 import inputs  # noqa: E402
+
+METRIC = "MP atoms/sec to 40 dB residual SNR, batched FP32 vs plain form; % HBM roofline"
+UNIT = "atoms/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(name):
+    cfg = inputs.WORKLOADS[name]
+    dicts = [(inputs.make_window(k, w), a, M) for (k, w, a, M) in cfg["dicts"]]
+    xs = inputs.workload_signal(name)
+    if not isinstance(xs, list):
+        xs = [xs]
+    return cfg, dicts, xs
+
+
+def _config_desc(name, cfg, xs):
+    return {
+        "workload": name,
+        "signals": len(xs),
+        "L_total": int(sum(len(x) for x in xs)),
+        "dicts": ["%s w=%d a=%d M=%d" % d for d in cfg["dicts"]],
+        "kern_thr": cfg["eps"],
+        "kmax": cfg["kmax"],
+        "target_snr_db": cfg["snr_db"],
+        "l2": "flushed between steps (%d MiB write)" % (L2_FLUSH_BYTES >> 20),
+    }
+
+
+# --------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [s.strip() for s in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ roofline -----
+
+def update_bytes(mg, plan, state, atoms_per_sig):
+    """Algorithmic bytes of the residual updates: for every selected atom and
+    every dictionary v, the stored coefficients covered by the atom's class
+    tile and by its conjugate partner's, each read and written once as
+    complex64 (16 bytes)."""
+    W = plan.W
+    infos = {}
+    for u in range(W):
+        for v in range(W):
+            i0 = mg.mp_plan_tile_info(plan, u, v, 0, 0)
+            for cf in range(i0["rf"]):
+                for ct in range(i0["rt"]):
+                    infos[(u, v, cf, ct)] = mg.mp_plan_tile_info(plan, u, v, cf, ct)
+    total = 0
+    for atoms in atoms_per_sig:
+        if atoms.size == 0:
+            continue
+        for u in range(W):
+            sel = atoms[atoms["dict"] == u]
+            if sel.size == 0:
+                continue
+            Mu, au = plan.M[u], plan.a[u]
+            ks = sel["m"].astype(np.int64)
+            js = sel["n"].astype(np.int64)
+            edge = (ks == 0) | (2 * ks == Mu)
+            for v in range(W):
+                Mv, av = plan.M[v], plan.a[v]
+                Mr = Mv // 2 + 1
+                rf = infos[(u, v, 0, 0)]["rf"]
+                rt = infos[(u, v, 0, 0)]["rt"]
+                ct = js % rt
+                for conj in (False, True):
+                    kk = (Mu - ks) if conj else ks
+                    cf = kk % rf
+                    base_m = kk * (Mv // Mu) if Mv >= Mu else (kk - cf) // rf
+                    R = np.array([infos[(u, v, int(a), int(b))]["R"] for a, b in zip(cf, ct)])
+                    C = np.array([infos[(u, v, int(a), int(b))]["C"] for a, b in zip(cf, ct)])
+                    ilo = np.array([infos[(u, v, int(a), int(b))]["i_lo"] for a, b in zip(cf, ct)])
+                    A = (base_m + ilo) % Mv
+                    p1 = np.clip(np.minimum(np.minimum(A + R, Mv), Mr) - A, 0, None)
+                    p2 = np.where(A + R > Mv, np.clip(np.minimum(A + R - Mv, Mr), 0, None), 0)
+                    n = (p1 + p2) * C
+                    if conj:
+                        n = np.where(edge, 0, n)
+                    total += int(n.sum()) * 16
+    return total
+
+
+def _profile_traffic(kernel_file, workload):
+    """dram bytes per launch of the MP loop from the committed ncu summary,
+    or None when the kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "mp_loop_%s.md" % workload)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not (m and t):
+        return None
+    cur = hashlib.sha256(open(kernel_file, "rb").read()).hexdigest()
+    return float(t.group(1)) if cur == m.group(1) else None
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------- GPU arm -----
+
+def run_gpu(args):
+    import torch
+
+    from paper_2202_12380_gb300 import mpgabor as mg
+
+    ws, rank, local = _dist()
+    dev = local if torch.cuda.device_count() > 1 else 0
+    torch.cuda.set_device(dev)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    cfg, dicts, xs = _workload(args.workload)
+    stream = torch.cuda.Stream()
+    plan = mg.mp_plan_create([d[0] for d in dicts], [d[1] for d in dicts], [d[2] for d in dicts],
+                             cfg["eps"], mg.MP_ANALYSIS_FP32, stream)
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    K, snr = cfg["kmax"], cfg["snr_db"]
+    state = None
+    W = len(dicts)
+
+    def one_step(ev):
+        nonlocal state
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            state = mg.mp_analyze(plan, xd, state)
+            ev[1].record(stream)
+            mg.mp_run_async(state, K, snr)
+            ev[2].record(stream)
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.zero_()
+
+    for _ in range(args.warmup):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        flush_l2()
+        one_step(ev)
+    stream.synchronize()
+    n0, _, _ = mg.mp_get_status(state)
+
+    launches_per_step = 1 + 2 * W + 1
+    clocks = ClockSampler(dev)
+    clocks.start()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        flush_l2()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        one_step(ev)
+        evs.append(ev)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    loop_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    ana_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    n_atoms, stops, snrs = mg.mp_get_status(state)
+    atoms_per_step = int(np.sum(n_atoms))
+    t_total = sum(step_ms) / 1e3
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+        na = torch.tensor([atoms_per_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(na)
+        total_atoms_all = float(na.item()) * args.steps
+    else:
+        total_atoms_all = float(atoms_per_step) * args.steps
+    value = total_atoms_all / t_total
+
+    # roofline of the MP loop kernel
+    atoms_list = [mg.mp_get_atoms(state, b) for b in range(len(xs))]
+    alg_bytes = update_bytes(mg, plan, state, atoms_list)
+    loop_s = float(np.mean(loop_ms)) / 1e3
+    achieved = alg_bytes / loop_s / 1e9
+    peak, peak_src = _peaks()
+    traffic = _profile_traffic(os.path.join(ROOT, "paper_2202_12380_gb300", "csrc", "mp_loop.cu"),
+                               args.workload)
+
+    # end to end through the C ABI with host buffers (pinned)
+    e2e = None
+    if args.e2e_steps > 0:
+        xh = [torch.from_numpy(x).pin_memory() for x in xs]
+        st_h = None
+        for _ in range(2):
+            st_h = mg.mp_analyze_host(plan, xh, st_h)
+            mg.mp_run(st_h, K, snr)
+            _ = [mg.mp_get_atoms(st_h, b) for b in range(len(xs))]
+        h2d = int(sum(x.numel() * 4 for x in xh))
+        d2h = 0
+        t0 = time.perf_counter()
+        tot = 0
+        for _ in range(args.e2e_steps):
+            st_h = mg.mp_analyze_host(plan, xh, st_h)
+            n, _, _ = mg.mp_run(st_h, K, snr)
+            got = [mg.mp_get_atoms(st_h, b) for b in range(len(xs))]
+            tot += int(sum(g.size for g in got))
+            d2h = int(sum(g.nbytes for g in got))
+        t1 = time.perf_counter()
+        e2e = {"value": tot / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
+        st_h.close()
+
+    batched = None
+    if args.batched and ws == 1:
+        batched = run_batched(args, mg, torch)
+
+    cpu = None
+    if rank == 0 and ws == 1 and args.cpu_baseline:
+        cpu = cpu_baseline(args.workload, args.cpu_atoms)
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": float(np.mean(step_ms)),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded mixture; the paper's audio is not available)",
+        "config": dict(_config_desc(args.workload, cfg, xs),
+                       parallelism="replicas" if ws > 1 else "single"),
+        "atoms_per_step": atoms_per_step,
+        "stop_reasons": [int(s) for s in stops[:8]],
+        "final_snr_db": [float(q) for q in snrs[:8]],
+        "analysis_ms": float(np.mean(ana_ms)),
+        "mp_loop_ms": float(np.mean(loop_ms)),
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": {"kernel": "k_mp_loop", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": peak_src,
+                     "alg_bytes_per_launch": alg_bytes,
+                     "alg_bytes_per_atom": alg_bytes / max(atoms_per_step, 1)},
+        "clocks": clk,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    if batched is not None:
+        line["batched"] = batched
+    if rank == 0:
+        print(json.dumps(line))
+    state.close()
+    plan.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_batched(args, mg, torch):
+    """Secondary figure: the batched form (256 uneven signals, one launch)."""
+    cfg, dicts, xs = _workload("batch256")
+    stream = torch.cuda.Stream()
+    plan = mg.mp_plan_create([d[0] for d in dicts], [d[1] for d in dicts], [d[2] for d in dicts],
+                             cfg["eps"], mg.MP_ANALYSIS_FP32, stream)
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    state = None
+    res = []
+    for it in range(args.batched_steps + 1):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        with torch.cuda.stream(stream):
+            e[0].record(stream)
+            state = mg.mp_analyze(plan, xd, state)
+            e[1].record(stream)
+            mg.mp_run_async(state, cfg["kmax"], cfg["snr_db"])
+            e[2].record(stream)
+        stream.synchronize()
+        if it > 0:
+            res.append((e[0].elapsed_time(e[2]), e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])))
+    n, stops, snrs = mg.mp_get_status(state)
+    atoms = [mg.mp_get_atoms(state, b) for b in range(len(xs))]
+    alg = update_bytes(mg, plan, state, atoms)
+    step = float(np.mean([r[0] for r in res]))
+    loop = float(np.mean([r[2] for r in res]))
+    peak, _ = _peaks()
+    out = {"workload": "batch256", "signals": len(xs), "L_total": int(sum(len(x) for x in xs)),
+           "atoms_per_step": int(n.sum()), "ms_per_step": step,
+           "analysis_ms": float(np.mean([r[1] for r in res])), "mp_loop_ms": loop,
+           "value": float(n.sum()) / (step / 1e3), "unit": UNIT,
+           "mp_loop_hbm_frac": alg / (loop / 1e3) / 1e9 / peak,
+           "stops": {str(k): int(v) for k, v in zip(*np.unique(stops, return_counts=True))}}
+    state.close()
+    plan.close()
+    return out
+
+
+# -------------------------------------------------------------- CPU arm -----
+
+def _oracle_sample(workload, atoms):
+    from oracle import cmp
+    cfg, dicts, xs = _workload(workload)
+    x = xs[0].astype(np.float64)
+    t0 = time.perf_counter()
+    res = cmp.mp_coef(dicts, x, cfg["eps"], atoms, cfg["snr_db"])
+    dt = time.perf_counter() - t0
+    return res.n_atoms, dt
+
+
+def cpu_baseline(workload, atoms):
+    n, dt = _oracle_sample(workload, atoms)
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "FP64 C oracle (coefficient-domain MP, 1 thread): analysis + first %d atoms "
+                      "of the %s signal, %.1f s" % (n, workload, dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    cfg, dicts, xs = _workload(args.workload)
+    for _ in range(args.warmup):
+        _oracle_sample(args.workload, max(args.ref_atoms // 10, 1))
+    tot_atoms, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        n, dt = _oracle_sample(args.workload, args.ref_atoms)
+        tot_atoms += n
+        tot_t += dt
+    value = tot_atoms / tot_t
+    sample = ("FP64 C oracle (coefficient-domain MP, 1 thread): analysis + first %d atoms of the "
+              "%s signal per step" % (args.ref_atoms, args.workload))
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_t / max(args.steps, 1),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded mixture; the paper's audio is not available)",
+        "config": dict(_config_desc(args.workload, cfg, xs), parallelism="single"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="multi3_2p18",
+                    choices=["multi3_2p18", "single_gauss_16k", "multi5_2p20"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--batched-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-atoms", type=int, default=50000)
+    ap.add_argument("--ref-atoms", type=int, default=10000)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()
