@@ -177,6 +177,38 @@ int mp_synthesize(const mp_state* state, int sig, float* y_dev, double* true_snr
 
 void mp_state_destroy(mp_state* state);
 
+/*
+ * Allocation-free decomposition of one signal (no counterpart in the paper:
+ * it is an operational variant of mp_analyze + mp_run).
+ *
+ * For callers that cannot call cudaMalloc while they decompose: work issued
+ * inside a CUDA stream capture (cudaMalloc is not a stream operation and
+ * breaks the capture), real-time audio threads that must not block on the
+ * device allocator (cudaMalloc may synchronise the device), and processes
+ * held to a fixed device-memory budget.  The plan is created beforehand (that
+ * call allocates); this call then allocates nothing: the coefficient planes,
+ * max trees and bookkeeping live in one file-scope device array of 32 MiB
+ * that every GPU loading the library holds until the process exits.
+ *   x_dev       device pointer to L floats (input)
+ *   atoms_dev   device buffer of K_max mp_atom (output, atoms in order)
+ *   errors_dev  device buffer of K_max doubles for E_k (output) or NULL
+ *   n_atoms, stop_reason, final_snr_db  host outputs or NULL; if all three
+ *               are NULL the call is asynchronous on the plan's stream,
+ *               otherwise it synchronises the stream and fills them
+ * Same method, kernels and results as mp_analyze + mp_run on one signal
+ * (no time limit).  Returns MP_EINVAL with a message if the signal needs
+ * more than the 32 MiB array (about L = 2^18 with three dictionaries of
+ * 512..2048 channels fits); use mp_analyze / mp_run for larger inputs.
+ * The first call on each device resolves the array's device address
+ * (cudaGetSymbolAddress) -- make that first call before any stream capture.
+ * All calls on a device share the array and each call rewrites every part
+ * of it it uses; calls that overlap on the GPU (other streams or threads)
+ * race on it and must be serialised by the caller.
+ */
+int mp_decompose_static(const mp_plan* plan, const float* x_dev, int64_t L, int64_t K_max,
+                        double target_snr_db, mp_atom* atoms_dev, double* errors_dev,
+                        int64_t* n_atoms, int* stop_reason, double* final_snr_db);
+
 /* message of the last failure on this host thread ("" if none) */
 const char* mp_last_error(void);
 

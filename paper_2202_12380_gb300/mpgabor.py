@@ -29,6 +29,7 @@ EXPORTS = [
     "mp_plan_tile_info", "mp_plan_tile", "mp_plan_gamma", "mp_analyze", "mp_analyze_host",
     "mp_state_coefficients", "mp_run", "mp_run_async", "mp_get_status", "mp_state_set_time_limit",
     "mp_get_atoms", "mp_get_errors", "mp_synthesize", "mp_state_destroy", "mp_last_error",
+    "mp_decompose_static",
 ]
 
 _lib = None
@@ -75,6 +76,7 @@ def lib():
         "mp_synthesize": ([vp, i32, vp, P(dbl)], i32),
         "mp_state_destroy": ([vp], None),
         "mp_last_error": ([], C.c_char_p),
+        "mp_decompose_static": ([vp, vp, i64, i64, dbl, vp, vp, P(i64), P(i32), P(dbl)], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -311,3 +313,29 @@ def mp_state_destroy(state: State):
 
 def mp_last_error() -> str:
     return lib().mp_last_error().decode(errors="replace")
+
+
+def mp_decompose_static(plan: Plan, x, K_max: int, target_snr_db: float, atoms_out, errors_out=None):
+    """Allocation-free analysis + MP of one signal (see include/mpgabor.h).
+
+    x: float32 CUDA tensor; atoms_out: CUDA tensor of at least K_max * 24
+    bytes (e.g. torch.empty(K_max * 24, dtype=torch.uint8)); errors_out:
+    float64 CUDA tensor of K_max entries or None.  Returns (n_atoms, stop,
+    snr_db); the atoms are read back with atoms_from_bytes()."""
+    if not (x.is_cuda and x.is_contiguous() and str(x.dtype) == "torch.float32"):
+        raise ValueError("x must be a contiguous float32 CUDA tensor")
+    if atoms_out.numel() * atoms_out.element_size() < int(K_max) * ATOM_DTYPE.itemsize:
+        raise ValueError("atoms_out is too small")
+    if errors_out is not None and errors_out.numel() < int(K_max):
+        raise ValueError("errors_out is too small")
+    n, s, q = C.c_int64(), C.c_int(), C.c_double()
+    _check(lib().mp_decompose_static(plan.handle, x.data_ptr(), int(x.numel()), int(K_max),
+                                     float(target_snr_db), atoms_out.data_ptr(),
+                                     errors_out.data_ptr() if errors_out is not None else None,
+                                     C.byref(n), C.byref(s), C.byref(q)))
+    return n.value, s.value, q.value
+
+
+def atoms_from_bytes(buf, n):
+    """View the first n records of a byte buffer (numpy) as mp_atom."""
+    return np.frombuffer(np.ascontiguousarray(buf).tobytes(), dtype=ATOM_DTYPE, count=int(n))
