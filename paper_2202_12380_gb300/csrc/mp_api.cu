@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstddef>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <vector>
@@ -243,7 +244,7 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
         state_free(s);
         return cuda_fail(e, "mp_analyze: state set-up");
     }
-    s->smem = mp_loop_smem_bytes(s->Tmax, W);
+    s->smem = mp_loop_smem_bytes(p->dp, s->Tmax);
     *out = s;
     return MP_OK;
 }
@@ -392,8 +393,13 @@ extern "C" int mp_run_async(mp_state* s, int64_t K_max, double target_snr_db) {
     const double thr_scale = std::pow(10.0, -target_snr_db / 10.0);
     const long long budget =
         s->time_limit_s > 0 ? (long long)std::min(s->time_limit_s * 1e9, 9e18) : 0LL;
+    int threads = mp_loop_threads(s->B, s->plan->num_sms);
+    if (const char* ov = getenv("MPGABOR_LOOP_THREADS")) {  // tuning override: 256, 512 or 1024
+        int t = atoi(ov);
+        if (t == 256 || t == 512 || t == 1024) threads = t;
+    }
     CKR(launch_mp_loop(s->plan->dp, s->d_sigs, s->d_order, s->B, K_max, thr_scale, budget, s->smem,
-                       s->plan->stream));
+                       threads, s->plan->stream));
     return MP_OK;
 }
 

@@ -31,13 +31,18 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long k)
     return k;
 }
 
-// warp-wide max Entry (key decides); every lane returns the winner
+// warp-wide max Entry (key decides); every lane returns the winner.  The
+// 64-bit key is reduced as two 32-bit redux steps (score word, then the
+// inverted index among the lanes holding the top score), which is a much
+// shorter dependent chain than a shuffle tree.
 __device__ __forceinline__ Entry warp_max_entry(Entry e) {
-    unsigned long long mk = warp_max_u64(e.key);
-    unsigned ball = __ballot_sync(FULL, e.key == mk);
-    int src = __ffs(ball) - 1;
+    const unsigned hi = (unsigned)(e.key >> 32), lo = (unsigned)e.key;
+    const unsigned mh = __reduce_max_sync(FULL, hi);
+    const unsigned ml = __reduce_max_sync(FULL, hi == mh ? lo : 0u);
+    const unsigned ball = __ballot_sync(FULL, hi == mh && lo == ml);
+    const int src = __ffs(ball) - 1;
     Entry r;
-    r.key = mk;
+    r.key = ((unsigned long long)mh << 32) | ml;
     r.val.x = __shfl_sync(FULL, e.val.x, src);
     r.val.y = __shfl_sync(FULL, e.val.y, src);
     return r;

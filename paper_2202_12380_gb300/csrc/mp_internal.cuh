@@ -55,6 +55,8 @@ struct DevClass {
 
 struct DevPlan {
     int W;
+    int ncls;  // class descriptors
+    int ngam;  // entries of the compact <d, conj d> pool
     int pad;
     DevDict d[MAXW];
     DevPair p[MAXW * MAXW];
@@ -101,13 +103,14 @@ cudaError_t launch_group_build(const DevSig* d_sigs, int nsig, const int* d_grou
                                long long total_groups, int W, cudaStream_t st);
 cudaError_t launch_mp_loop(const DevPlan& P, DevSig* d_sigs, const int* d_order, int nsig,
                            long long kmax, double thr_scale, long long budget_ns, size_t smem,
-                           cudaStream_t st);
+                           int threads, cudaStream_t st);
 cudaError_t launch_synth(const DevPlan& P, const DevSig* d_sig, long long natoms, float* y,
                          long long L, cudaStream_t st);
 cudaError_t launch_resid_energy(const DevSig* d_sig, const float* y, long long L,
                                 double* d_partials, int nparts, cudaStream_t st);
 
-size_t mp_loop_smem_bytes(int T, int W);
+size_t mp_loop_smem_bytes(const DevPlan& P, int T);
+int mp_loop_threads(int nsig, int num_sms);
 
 }  // namespace mpg
 
@@ -125,6 +128,7 @@ struct mp_plan {
     unsigned flags;
     cudaStream_t stream;
     int device;
+    int num_sms;
     mpg::DevPlan dp;  // device view (pointers below)
     // geometry of every ordered pair (u, v), index u * W + v
     int Mx[mpg::MAXW * mpg::MAXW], an[mpg::MAXW * mpg::MAXW];

@@ -3,20 +3,28 @@
 // -> energy bookkeeping -> coefficient-domain update of every dictionary ->
 // max-tree repair, entirely on the device.
 //
-// Selection (Sec. 5.1).  The top level of the max tree (one Entry per frame,
-// or per group of 2^gshift frames) and a level of "super" entries (one per
-// 32 top entries) live in shared memory; warp 0 reduces the supers.  Level 0
-// (per frame and 32-bin chunk) and level 1 (per frame) live in global memory
-// next to the coefficient planes.
+// Max tree (Sec. 5.1).  Level 0 (per frame and 32-bin chunk) and level 1
+// (per frame) live in global memory next to the coefficient planes; the top
+// level (one Entry per frame, or per group of 2^gshift frames) lives in
+// shared memory and is scanned by the whole CTA every iteration (a few
+// shared loads per thread), so there is no further level to maintain.
 //
-// Update (eqs. fastkernupdate, hkj, Alg. 3).  For the selected (u, k, j) and
-// each dictionary v, the atom and (for 0 < k < M_u/2) its conjugate partner
-// (M_u - k, conj(c)) each hit one dense class tile of h_{u,v}; the tile's
-// rows wrap mod M_v and only rows 0..M_v/2 are stored, its columns wrap mod
-// N_v.  The work is cut into warp jobs of (frame, 32-bin chunk): each lane
-// owns one bin, applies both terms, and the warp recomputes the chunk's
-// level-0 entry on the spot.  Frames touched are then re-reduced from level
-// 0, groups from level 1, supers from the top level.
+// One iteration, for every warp of the CTA:
+//   1. scan the top level, warp-reduce, publish the warp's best; barrier;
+//   2. reduce the per-warp bests (every warp redundantly), apply the stop
+//      tests, adjust the selected coefficient to the real-pair coefficient
+//      (eqs. dualatprod / projenfaster), accumulate E in FP64 and describe
+//      the update of every dictionary: lane 2v + t builds term t (0: the
+//      atom, 1: its conjugate partner) of dictionary v;
+//   3. run frame jobs: for each touched frame of each dictionary, load the
+//      frame's level-0 entries together with the touched 32-bin chunks of the
+//      plane and the matching class-tile entries (one round of independent
+//      loads), subtract both terms (eq. fastkernupdate with the modulation of
+//      eq. hkj), recompute the touched chunks' level-0 entries, the frame's
+//      level-1 entry and its top-level slot; barrier.
+// Every warp computes the same selection; thread 0 alone writes the atom list
+// and keeps the FP64 energy E, whose stop tests it publishes for the next
+// iteration before the closing barrier.
 #include <cuda_runtime.h>
 
 #include "mp_common_dev.cuh"
@@ -25,8 +33,10 @@
 namespace mpg {
 namespace {
 
-constexpr int NWARPS = LOOP_THREADS / 32;
+constexpr int MAXL0 = 4;   // level-0 entries held per lane (larger frames loop)
+constexpr int CB = 4;      // touched chunks processed per batch of loads
 
+// one term (the atom or its conjugate partner) of the update of dictionary v
 struct Term {
     int active;
     int Arow;   // first tile row, as a bin of dictionary v, in [0, M_v)
@@ -35,29 +45,8 @@ struct Term {
     int C;
     int kk;     // frequency index (in dictionary u) of this atom
     int tau0;   // tau of tile column 0
-    float2 coef;
-    const float2* tile;
-};
-
-struct VJob {
-    Term t[2];
-    long long nstart;  // first frame of the column hull (wrapped)
-    int ncols;
-    int nr;            // chunk ranges [cr0, cr1)
-    int cr0[4], cr1[4];
-    int nchunks;
-    int njobs, jbase;  // update jobs and their prefix
-    int fbase;         // prefix of frame jobs
-};
-
-struct Shared {
-    VJob vj[MAXW];
-    Entry win;
-    int u, kk;
-    long long j;
-    int stop;
-    int total_jobs, total_frames;
-    int S;  // number of supers
+    int a0;     // unwrapped first column (for the column hull)
+    long long tile;  // float2 offset of the class tile
 };
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -70,307 +59,405 @@ __device__ __forceinline__ unsigned long long gtimer() {
     return t;
 }
 
-// rows of a term inside the stored range [0, Mr): up to two intervals
-__device__ void term_rows(const Term& t, int Mv, int Mr, int* lo, int* hi, int* n) {
-    *n = 0;
-    int e1 = min(t.Arow + t.R, Mv);
-    int a0 = t.Arow, a1 = min(e1, Mr);
-    if (a1 > a0) { lo[*n] = a0; hi[*n] = a1; ++*n; }
-    if (t.Arow + t.R > Mv) {
-        int b1 = min(t.Arow + t.R - Mv, Mr);
-        if (b1 > 0) { lo[*n] = 0; hi[*n] = b1; ++*n; }
-    }
+__device__ __forceinline__ int imod(int x, int m) {
+    int r = x % m;
+    return r < 0 ? r + m : r;
 }
 
-// describe the update of dictionary v for selected (u, k, j) with coefficient c
-__device__ void make_vjob(const DevPlan& P, const DevSig& S, int u, int k, long long j, float2 c,
-                          bool edge, int v, VJob& J) {
-    const DevDict& Du = P.d[u];
-    const DevDict& Dv = P.d[v];
-    const DevPair& PR = P.p[u * P.W + v];
+__device__ __forceinline__ Term shfl_term(const Term& t, int src) {
+    Term r;
+    r.active = __shfl_sync(FULL, t.active, src);
+    r.Arow = __shfl_sync(FULL, t.Arow, src);
+    r.R = __shfl_sync(FULL, t.R, src);
+    r.Acol = __shfl_sync(FULL, t.Acol, src);
+    r.C = __shfl_sync(FULL, t.C, src);
+    r.kk = __shfl_sync(FULL, t.kk, src);
+    r.tau0 = __shfl_sync(FULL, t.tau0, src);
+    r.a0 = __shfl_sync(FULL, t.a0, src);
+    r.tile = __shfl_sync(FULL, t.tile, src);
+    return r;
+}
+
+// term t of dictionary v for the selected (u, k, j)
+__device__ __forceinline__ Term make_term(const DevDict* sd, const DevPair* sp,
+                                          const DevClass* scls, int W, const DevSig& S, int u,
+                                          int k, int j, bool edge, int v, int t) {
+    Term T;
+    T.active = 0;
+    T.Arow = T.R = T.Acol = T.C = T.kk = T.tau0 = T.a0 = 0;
+    T.tile = 0;
+    if (t == 1 && edge) return T;
+    const DevDict& Du = sd[u];
+    const DevDict& Dv = sd[v];
+    const DevPair& PR = sp[u * W + v];
     const int Mu = Du.M, Mv = Dv.M, au = Du.a, av = Dv.a;
-    const long long Nv = S.N[v];
-    const int ct = (int)(j % PR.rt);
-    const long long base_n = (av <= au) ? j * (au / av) : (j - ct) / PR.rt;
-    int rlo[4], rhi[4], nrng = 0;
-    long long cmin = 0, cmax = 0;
-    bool any = false;
-    for (int ti = 0; ti < 2; ++ti) {
-        Term& T = J.t[ti];
-        T.active = 0;
-        if (ti == 1 && edge) continue;
-        const int kk = ti == 0 ? k : Mu - k;
-        const int cf = kk % PR.rf;
-        const long long base_m = (Mv >= Mu) ? (long long)kk * (Mv / Mu) : (kk - cf) / PR.rf;
-        const DevClass& C = P.cls[PR.cls_base + cf * PR.rt + ct];
-        if (C.R == 0) continue;
-        T.Arow = (int)lmod(base_m + C.i_lo, Mv);
-        T.R = C.R;
-        T.C = C.C;
-        T.kk = kk;
-        T.tau0 = C.c_lo * av - ct * au;
-        T.coef = ti == 0 ? c : make_float2(c.x, -c.y);
-        T.tile = P.tiles + C.off;
-        int lo[2], hi[2], nn;
-        term_rows(T, Mv, Dv.Mr, lo, hi, &nn);
-        if (nn == 0) continue;
-        T.active = 1;
-        for (int q = 0; q < nn; ++q) {
-            rlo[nrng] = lo[q] / CHUNK;
-            rhi[nrng] = (hi[q] - 1) / CHUNK + 1;
-            ++nrng;
-        }
-        long long a0 = base_n + C.c_lo;
-        T.Acol = (int)lmod(a0, Nv);
-        if (!any) { cmin = a0; cmax = a0 + C.C; any = true; }
-        else { cmin = min(cmin, a0); cmax = max(cmax, a0 + (long long)C.C); }
-    }
-    J.nr = 0;
-    J.nchunks = 0;
-    J.ncols = 0;
-    J.nstart = 0;
-    if (!any) return;
-    // merge chunk ranges (at most 4) into disjoint sorted ranges
-    for (int a = 1; a < nrng; ++a)
-        for (int b = a; b > 0 && rlo[b] < rlo[b - 1]; --b) {
-            int t0 = rlo[b]; rlo[b] = rlo[b - 1]; rlo[b - 1] = t0;
-            int t1 = rhi[b]; rhi[b] = rhi[b - 1]; rhi[b - 1] = t1;
-        }
-    for (int a = 0; a < nrng; ++a) {
-        if (J.nr > 0 && rlo[a] <= J.cr1[J.nr - 1]) {
-            J.cr1[J.nr - 1] = max(J.cr1[J.nr - 1], rhi[a]);
-        } else {
-            J.cr0[J.nr] = rlo[a];
-            J.cr1[J.nr] = rhi[a];
-            ++J.nr;
-        }
-    }
-    for (int a = 0; a < J.nr; ++a) J.nchunks += J.cr1[a] - J.cr0[a];
-    long long ncols = cmax - cmin;
-    if (ncols >= Nv) { J.nstart = 0; J.ncols = (int)Nv; }
-    else { J.nstart = lmod(cmin, Nv); J.ncols = (int)ncols; }
+    const int kk = t == 0 ? k : Mu - k;
+    const int ct = j % PR.rt;
+    const int cf = kk % PR.rf;
+    const DevClass& C = scls[PR.cls_base + cf * PR.rt + ct];
+    if (C.R == 0) return T;
+    const int base_m = (Mv >= Mu) ? kk * (Mv / Mu) : (kk - cf) / PR.rf;
+    const int base_n = (av <= au) ? j * (au / av) : (j - ct) / PR.rt;
+    T.Arow = imod(base_m + C.i_lo, Mv);
+    T.R = C.R;
+    // any stored row (0 .. M_v/2) inside [Arow, Arow + R) mod M_v ?
+    const bool rows = (T.Arow < Dv.Mr) || (T.Arow + T.R > Mv);
+    if (!rows) return T;
+    T.active = 1;
+    T.C = C.C;
+    T.kk = kk;
+    T.tau0 = C.c_lo * av - ct * au;
+    T.a0 = base_n + C.c_lo;
+    T.Acol = imod(T.a0, (int)S.N[v]);
+    T.tile = C.off;
+    return T;
 }
 
-__device__ __forceinline__ float2 gamma_of(const DevPlan& P, int u, int k) {
-    const DevDict& D = P.d[u];
-    if (k < D.gam_lo) return P.gam[D.gam_off + k];
-    if (k >= D.Mr - D.gam_hi) return P.gam[D.gam_off + D.gam_lo + (k - (D.Mr - D.gam_hi))];
+// chunk ranges [lo, hi) of a term's stored rows: up to two
+__device__ __forceinline__ int term_chunks(const Term& t, int Mv, int Mr, int* lo, int* hi) {
+    if (!t.active) return 0;
+    int n = 0;
+    const int e1 = min(min(t.Arow + t.R, Mv), Mr);
+    if (e1 > t.Arow) { lo[n] = t.Arow / CHUNK; hi[n] = (e1 - 1) / CHUNK + 1; ++n; }
+    if (t.Arow + t.R > Mv) {
+        const int b1 = min(t.Arow + t.R - Mv, Mr);
+        if (b1 > 0) { lo[n] = 0; hi[n] = (b1 - 1) / CHUNK + 1; ++n; }
+    }
+    return n;
+}
+
+__device__ __forceinline__ bool term_hit(const Term& T, int m, int n, int Mv, int Nv, int* off) {
+    if (!T.active) return false;
+    int cc = n - T.Acol;
+    if (cc < 0) cc += Nv;
+    if (cc >= T.C) return false;
+    int i = m - T.Arow;
+    if (i < 0) i += Mv;
+    if (i >= T.R) return false;
+    *off = cc * T.R + i;
+    return true;
+}
+
+__device__ __forceinline__ float2 term_phase(const Term& T, int n, int Nv, int av, int Mu) {
+    int cc = n - T.Acol;
+    if (cc < 0) cc += Nv;
+    const int tau = T.tau0 + cc * av;
+    const unsigned tm = (unsigned)imod(tau, Mu);
+    const unsigned q = ((unsigned)T.kk * tm) % (unsigned)Mu;
+    float sn, cs;
+    sincospif(2.0f * (float)q / (float)Mu, &sn, &cs);
+    return make_float2(cs, sn);
+}
+
+__device__ __forceinline__ float2 gamma_of(const DevDict& D, const float2* sgam, int k) {
+    if (k < D.gam_lo) return sgam[D.gam_off + k];
+    if (k >= D.Mr - D.gam_hi) return sgam[D.gam_off + D.gam_lo + (k - (D.Mr - D.gam_hi))];
     return make_float2(0.f, 0.f);
 }
 
-__global__ void __launch_bounds__(LOOP_THREADS, 1)
+template <int NT>
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
     k_mp_loop(DevPlan P, DevSig* __restrict__ sigs, const int* __restrict__ order,
               long long kmax, double thr_scale, long long budget_ns) {
+    constexpr int NWARPS = NT / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ Shared sh;
     __shared__ DevSig S;
+    __shared__ DevDict sd[MAXW];
+    __shared__ DevPair sp[MAXW * MAXW];
+    __shared__ Entry wbest[NWARPS];
+    __shared__ int sstop[2];  // stop decision per iteration parity
     DevSig& Sg = sigs[order[blockIdx.x]];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     {
         const int* src = reinterpret_cast<const int*>(&Sg);
         int* dst = reinterpret_cast<int*>(&S);
-        for (int i = tid; i < (int)(sizeof(DevSig) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+        for (int i = tid; i < (int)(sizeof(DevSig) / sizeof(int)); i += NT) dst[i] = src[i];
     }
-    __syncthreads();
     const int W = P.W;
+    for (int i = tid; i < W; i += NT) sd[i] = P.d[i];
+    for (int i = tid; i < W * W; i += NT) sp[i] = P.p[i];
+    __syncthreads();
     const int T = S.T;
-    const int NS = (T + 31) >> 5;
     Entry* top = reinterpret_cast<Entry*>(smem_raw);
-    Entry* sup = top + T;
-    unsigned char* tdirty = reinterpret_cast<unsigned char*>(sup + NS);
-    unsigned char* sdirty = tdirty + T;
+    DevClass* scls = reinterpret_cast<DevClass*>(top + T);
+    float2* sgam = reinterpret_cast<float2*>(scls + P.ncls);
+    unsigned char* tdirty = reinterpret_cast<unsigned char*>(sgam + P.ngam);
 
-    // load the top level and build the supers
+    for (int i = tid; i < P.ncls; i += NT) scls[i] = P.cls[i];
+    for (int i = tid; i < P.ngam; i += NT) sgam[i] = P.gam[i];
     for (int w = 0; w < W; ++w) {
         const int tb = S.tbase[w], te = S.tbase[w + 1];
         const Entry* src = S.gshift == 0 ? S.l1[w] : S.grp + tb;
-        for (int i = tid; i < te - tb; i += blockDim.x) top[tb + i] = src[i];
+        for (int i = tid; i < te - tb; i += NT) top[tb + i] = src[i];
     }
-    for (int i = tid; i < T; i += blockDim.x) tdirty[i] = 0;
-    for (int i = tid; i < NS; i += blockDim.x) sdirty[i] = 0;
-    __syncthreads();
-    for (int s = warp; s < NS; s += NWARPS) {
-        Entry e;
-        int i = s * 32 + lane;
-        if (i < T) e = top[i]; else { e.key = 0; e.val = make_float2(0.f, 0.f); }
-        Entry r = warp_max_entry(e);
-        if (lane == 0) sup[s] = r;
-    }
-    if (tid == 0) sh.S = NS;
+    for (int i = tid; i < T; i += NT) tdirty[i] = 0;
     __syncthreads();
 
     long long k = S.k;
+    // FP64 work stays in thread 0 (the FP64 pipe is narrow on this part):
+    // E, and the stop tests that read it, are evaluated there one iteration
+    // ahead and published in sstop
     double E = S.E;
     const double E0 = S.E0;
     const double thr = E0 * thr_scale;
     const unsigned long long t_start = gtimer();
+    const float2* __restrict__ tiles = P.tiles;
+    int stop = 0;
+    if (tid == 0) {
+        int s0 = 0;
+        if (!isfinite(E0)) s0 = MP_STOP_INVALID;
+        else if (E <= 0.0) s0 = MP_STOP_NEGENERGY;
+        else if (E <= thr) s0 = MP_STOP_SNR;
+        else if (k >= kmax) s0 = MP_STOP_KMAX;
+        sstop[k & 1] = s0;
+    }
+    __syncthreads();
 
     for (;;) {
-        // ---- selection, adjustment, bookkeeping (warp 0) ----------------
-        if (warp == 0) {
+        // ---- 1. scan of the top level ------------------------------------
+        {
             Entry b;
             b.key = 0;
             b.val = make_float2(0.f, 0.f);
-            for (int i = lane; i < NS; i += 32) {
-                Entry e = sup[i];
+            for (int i = tid; i < T; i += NT) {
+                const Entry e = top[i];
                 if (e.key > b.key) b = e;
             }
-            Entry best = warp_max_entry(b);
-            int stop = 0;
-            if (!isfinite(E0)) stop = MP_STOP_INVALID;
-            else if (E <= 0.0) stop = MP_STOP_NEGENERGY;
-            else if (E <= thr) stop = MP_STOP_SNR;
-            else if (k >= kmax) stop = MP_STOP_KMAX;
-            else if (budget_ns > 0 && (long long)(gtimer() - t_start) > budget_ns) stop = -1;
-            else if ((unsigned)(best.key >> 32) == 0u) stop = MP_STOP_ZEROMAX;
-            int u = 0, kk = 0;
-            long long j = 0;
-            float2 c = make_float2(0.f, 0.f);
-            bool edge = false;
-            if (stop == 0) {
-                const unsigned flat = 0xffffffffu - (unsigned)(best.key & 0xffffffffull);
-                while (u + 1 < W && S.fbase[u + 1] <= flat) ++u;
-                const int Mr = P.d[u].Mr;
-                const unsigned rel = flat - S.fbase[u];
-                j = rel / (unsigned)Mr;
-                kk = (int)(rel - (unsigned)j * (unsigned)Mr);
-                const int Mu = P.d[u].M;
-                edge = (kk == 0) || (2 * kk == Mu);
-                // eqs. dualatprod / projenfaster in FP64
-                double rx = best.val.x, ry = best.val.y, cx, cy, Ed;
-                if (edge) {
-                    cx = rx;
-                    cy = 0.0;
-                    Ed = rx * rx;
-                } else {
-                    float2 g = gamma_of(P, u, kk);
-                    double gx = g.x, gy = g.y;
-                    double den = 1.0 - (gx * gx + gy * gy);
-                    // rho - conj(gamma) conj(rho)
-                    double nx = rx - (gx * rx + gy * ry);
-                    double ny = ry - (gy * rx - gx * ry);
-                    cx = nx / den;
-                    cy = ny / den;
-                    Ed = 2.0 * (cx * cx + cy * cy + gx * (cx * cx - cy * cy) - 2.0 * gy * cx * cy);
-                }
-                E -= Ed;
-                c = make_float2((float)cx, (float)cy);
-                if (lane == 0) {
-                    mp_atom at;
-                    at.dict = u;
-                    at.m = kk;
-                    at.n = j;
-                    at.re = c.x;
-                    at.im = c.y;
-                    S.atoms[k] = at;
-                    S.errs[k] = E;
-                }
-            }
-            if (lane < W && stop == 0) make_vjob(P, S, u, kk, j, c, edge, lane, sh.vj[lane]);
-            __syncwarp();
-            if (lane == 0) {
-                sh.stop = stop;
-                sh.u = u;
-                sh.kk = kk;
-                sh.j = j;
-                int jb = 0, fb = 0;
-                if (stop == 0)
-                    for (int v = 0; v < W; ++v) {
-                        VJob& J = sh.vj[v];
-                        J.njobs = J.ncols * J.nchunks;
-                        J.jbase = jb;
-                        J.fbase = fb;
-                        jb += J.njobs;
-                        fb += J.nchunks > 0 ? J.ncols : 0;
-                    }
-                sh.total_jobs = jb;
-                sh.total_frames = fb;
-            }
+            const Entry r = warp_max_entry(b);
+            if (lane == 0) wbest[warp] = r;
+            // the time limit is read once per iteration by one thread so that
+            // every warp takes the same decision
+            if (tid == 0 && sstop[k & 1] == 0 && budget_ns > 0 &&
+                (long long)(gtimer() - t_start) > budget_ns)
+                sstop[k & 1] = -1;
         }
         __syncthreads();
-        if (sh.stop) break;
+
+        // ---- 2. selection, adjustment, update description (every warp) --
+        Entry best;
+        {
+            Entry b;
+            b.key = 0;
+            b.val = make_float2(0.f, 0.f);
+            if (lane < NWARPS) b = wbest[lane];
+            best = warp_max_entry(b);
+        }
+        stop = sstop[k & 1];
+        if (stop == 0 && (unsigned)(best.key >> 32) == 0u) stop = MP_STOP_ZEROMAX;
+        if (stop) break;
+
+        const unsigned flat = 0xffffffffu - (unsigned)(best.key & 0xffffffffull);
+        int u = 0;
+        while (u + 1 < W && S.fbase[u + 1] <= flat) ++u;
+        const int Mr_u = sd[u].Mr;
+        const unsigned rel = flat - S.fbase[u];
+        const int j = (int)(rel / (unsigned)Mr_u);
+        const int kk = (int)(rel - (unsigned)j * (unsigned)Mr_u);
+        const int Mu = sd[u].M;
+        const bool edge = (kk == 0) || (2 * kk == Mu);
+        // eqs. dualatprod / projenfaster: coefficient and energy drop in FP32
+        // (gamma is zero away from m = 0 and m = M/2), E accumulated in FP64
+        const float rx = best.val.x, ry = best.val.y;
+        float cx, cy, Edf;
+        if (edge) {
+            cx = rx;
+            cy = 0.f;
+            Edf = rx * rx;
+        } else {
+            const float2 g = gamma_of(sd[u], sgam, kk);
+            if (g.x == 0.f && g.y == 0.f) {
+                cx = rx;
+                cy = ry;
+                Edf = 2.f * fmaf(cx, cx, cy * cy);
+            } else {
+                const float inv = 1.f / (1.f - fmaf(g.x, g.x, g.y * g.y));
+                cx = (rx - fmaf(g.x, rx, g.y * ry)) * inv;   // rho - conj(gamma) conj(rho)
+                cy = (ry - fmaf(g.y, rx, -g.x * ry)) * inv;
+                const float c2 = fmaf(cx, cx, cy * cy), d2 = fmaf(cx, cx, -cy * cy);
+                Edf = 2.f * (c2 + fmaf(g.x, d2, -2.f * g.y * cx * cy));
+            }
+        }
+        if (tid == 0) {
+            E -= (double)Edf;
+            mp_atom at;
+            at.dict = u;
+            at.m = kk;
+            at.n = j;
+            at.re = cx;
+            at.im = cy;
+            S.atoms[k] = at;
+            S.errs[k] = E;
+            int s1 = 0;  // stop tests before the next selection
+            if (E <= 0.0) s1 = MP_STOP_NEGENERGY;
+            else if (E <= thr) s1 = MP_STOP_SNR;
+            else if (k + 1 >= kmax) s1 = MP_STOP_KMAX;
+            sstop[(k + 1) & 1] = s1;
+        }
         ++k;
-
-        // ---- coefficient-domain update + level 0 -------------------------
-        const int tj = sh.total_jobs;
-        for (int g = warp; g < tj; g += NWARPS) {
-            int v = 0;
-            while (v + 1 < W && sh.vj[v + 1].jbase <= g) ++v;
-            const VJob& J = sh.vj[v];
-            const DevDict& Dv = P.d[v];
-            const long long Nv = S.N[v];
-            const int local = g - J.jbase;
-            const int col = local / J.nchunks;
-            int ci = local - col * J.nchunks;
-            int r = 0;
-            while (ci >= J.cr1[r] - J.cr0[r]) { ci -= J.cr1[r] - J.cr0[r]; ++r; }
-            const int chunk = J.cr0[r] + ci;
-            const long long n = lmod(J.nstart + col, Nv);
-            const int m = chunk * CHUNK + lane;
-            float2* p = S.plane[v] + n * Dv.Mrp + m;
-            float2 val = *p;
-            bool mod = false;
-            if (m < Dv.Mr) {
-#pragma unroll
-                for (int ti = 0; ti < 2; ++ti) {
-                    const Term& T = J.t[ti];
-                    if (!T.active) continue;
-                    long long cc = n - T.Acol;
-                    if (cc < 0) cc += Nv;
-                    if (cc >= T.C) continue;
-                    int i = m - T.Arow;
-                    if (i < 0) i += Dv.M;
-                    if (i >= T.R) continue;
-                    const float2 h = __ldg(T.tile + cc * T.R + i);
-                    // modulation of eq. hkj for this column: e^{i 2 pi kk tau / M_u}
-                    const int Mu = P.d[sh.u].M;
-                    const long long tau = T.tau0 + cc * Dv.a;
-                    const long long q = lmod((long long)T.kk * tau, Mu);
-                    float sn, cs;
-                    sincospif(2.0f * (float)q / (float)Mu, &sn, &cs);
-                    const float2 ph = make_float2(cs, sn);
-                    const float2 d = cmul(T.coef, cmul(ph, h));
-                    val.x -= d.x;
-                    val.y -= d.y;
-                    mod = true;
+        const float2 c_main = make_float2(cx, cy), c_conj = make_float2(cx, -cy);
+        // lane 2v + t describes term t of dictionary v
+        Term mine;
+        {
+            const int v = lane >> 1, t = lane & 1;
+            if (v < W) {
+                mine = make_term(sd, sp, scls, W, S, u, kk, j, edge, v, t);
+            } else {
+                mine.active = 0;
+                mine.Arow = mine.R = mine.Acol = mine.C = mine.kk = mine.tau0 = mine.a0 = 0;
+                mine.tile = 0;
+            }
+        }
+        // frame counts per dictionary: column hull of its active terms
+        int nframes = 0, nstart = 0;  // meaningful in lanes 2v
+        {
+            const int oa = __shfl_xor_sync(FULL, mine.active, 1);
+            const int oa0 = __shfl_xor_sync(FULL, mine.a0, 1);
+            const int oc = __shfl_xor_sync(FULL, mine.C, 1);
+            if ((lane & 1) == 0 && (lane >> 1) < W) {
+                int lo = 0, hi = 0;
+                bool any = false;
+                if (mine.active) { lo = mine.a0; hi = mine.a0 + mine.C; any = true; }
+                if (oa) {
+                    if (any) { lo = min(lo, oa0); hi = max(hi, oa0 + oc); }
+                    else { lo = oa0; hi = oa0 + oc; any = true; }
+                }
+                if (any) {
+                    const int Nv = (int)S.N[lane >> 1];
+                    const int nc = hi - lo;
+                    if (nc >= Nv) { nstart = 0; nframes = Nv; }
+                    else { nstart = imod(lo, Nv); nframes = nc; }
                 }
             }
-            if (mod) *p = val;
-            Entry e;
-            e.val = val;
-            e.key = (m < Dv.Mr) ? make_key(val, S.fbase[v] + (unsigned)(n * Dv.Mr) + m) : 0ull;
-            Entry rr = warp_max_entry(e);
-            if (lane == 0) S.l0[v][n * Dv.nch + chunk] = rr;
         }
-        __syncthreads();
+        // inclusive prefix of frame counts over v (held in lanes 0, 2, 4, ...)
+        int pre = nframes;
+#pragma unroll
+        for (int o = 2; o < 2 * MAXW; o <<= 1) {
+            const int x = __shfl_up_sync(FULL, pre, o);
+            if (lane >= o) pre += x;
+        }
+        const int total = __shfl_sync(FULL, pre, 2 * W - 2);
 
-        // ---- level 1 of touched frames -----------------------------------
-        const int tf = sh.total_frames;
-        for (int g = warp; g < tf; g += NWARPS) {
-            // last dictionary whose prefix is <= g (it always has frames)
+        // ---- 3. frame jobs -------------------------------------------------
+        for (int g = warp; g < total; g += NWARPS) {
+            // dictionary: number of inclusive prefixes <= g
             int v = 0;
-            while (v + 1 < W && sh.vj[v + 1].fbase <= g) ++v;
-            const VJob& J = sh.vj[v];
-            const DevDict& Dv = P.d[v];
-            const long long n = lmod(J.nstart + (g - J.fbase), S.N[v]);
-            const Entry* l0 = S.l0[v] + n * Dv.nch;
-            Entry b;
-            b.key = 0;
-            b.val = make_float2(0.f, 0.f);
-            for (int c = lane; c < Dv.nch; c += 32) {
-                Entry e = l0[c];
+            for (int q = 0; q < W; ++q) {
+                const int pq = __shfl_sync(FULL, pre, 2 * q);
+                v += (pq <= g) ? 1 : 0;
+            }
+            const int pv = __shfl_sync(FULL, pre, 2 * v);
+            const int fv = __shfl_sync(FULL, nframes, 2 * v);
+            const int sv = __shfl_sync(FULL, nstart, 2 * v);
+            const Term t0 = shfl_term(mine, 2 * v);
+            const Term t1 = shfl_term(mine, 2 * v + 1);
+            const DevDict& Dv = sd[v];
+            const int Nv = (int)S.N[v];
+            int n = sv + (g - (pv - fv));
+            if (n >= Nv) n -= Nv;
+            // level-0 entries of the whole frame (untouched chunks keep theirs)
+            const Entry* l0row = S.l0[v] + (long long)n * Dv.nch;
+            Entry l0v[MAXL0];
+#pragma unroll
+            for (int q = 0; q < MAXL0; ++q) {
+                const int c = lane + 32 * q;
+                if (c < Dv.nch) l0v[q] = l0row[c];
+            }
+            // chunk list: the atom's ranges, then the partner's outside them
+            int lo[4], hi[4];
+            const int nr0 = term_chunks(t0, Dv.M, Dv.Mr, lo, hi);
+            const int nr1 = term_chunks(t1, Dv.M, Dv.Mr, lo + nr0, hi + nr0);
+            const int nr = nr0 + nr1;
+            float2* prow = S.plane[v] + (long long)n * Dv.Mrp;
+            const float2 w0 =
+                t0.active ? cmul(c_main, term_phase(t0, n, Nv, Dv.a, Mu)) : make_float2(0.f, 0.f);
+            const float2 w1 =
+                t1.active ? cmul(c_conj, term_phase(t1, n, Nv, Dv.a, Mu)) : make_float2(0.f, 0.f);
+            Entry fmax;
+            fmax.key = 0;
+            fmax.val = make_float2(0.f, 0.f);
+            // walk the chunks of ranges 0..nr-1, skipping partner chunks that
+            // the atom's ranges already cover
+            int r = 0, c = nr > 0 ? lo[0] : 0;
+            while (r < nr) {
+                int chunk[CB];
+                int cnt = 0;
+                while (cnt < CB && r < nr) {
+                    bool dup = false;
+                    if (r >= nr0)
+                        for (int q = 0; q < nr0; ++q) dup |= (c >= lo[q] && c < hi[q]);
+                    if (!dup) chunk[cnt++] = c;
+                    if (++c >= hi[r]) {
+                        ++r;
+                        if (r < nr) c = lo[r];
+                    }
+                }
+                float2 val[CB], h0[CB], h1[CB];
+                bool hit0[CB], hit1[CB];
+#pragma unroll
+                for (int q = 0; q < CB; ++q) {
+                    hit0[q] = hit1[q] = false;
+                    if (q < cnt) {
+                        const int m = chunk[q] * CHUNK + lane;
+                        val[q] = prow[m];
+                        int off;
+                        if (m < Dv.Mr) {
+                            if (term_hit(t0, m, n, Dv.M, Nv, &off)) {
+                                hit0[q] = true;
+                                h0[q] = __ldg(tiles + t0.tile + off);
+                            }
+                            if (term_hit(t1, m, n, Dv.M, Nv, &off)) {
+                                hit1[q] = true;
+                                h1[q] = __ldg(tiles + t1.tile + off);
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < CB; ++q) {
+                    if (q >= cnt) continue;
+                    const int m = chunk[q] * CHUNK + lane;
+                    float2 x2 = val[q];
+                    if (hit0[q]) {
+                        const float2 d = cmul(w0, h0[q]);
+                        x2.x -= d.x;
+                        x2.y -= d.y;
+                    }
+                    if (hit1[q]) {
+                        const float2 d = cmul(w1, h1[q]);
+                        x2.x -= d.x;
+                        x2.y -= d.y;
+                    }
+                    if (hit0[q] || hit1[q]) prow[m] = x2;
+                    Entry e;
+                    e.val = x2;
+                    e.key = (m < Dv.Mr) ? make_key(x2, S.fbase[v] + (unsigned)n * Dv.Mr + m) : 0ull;
+                    const Entry rr = warp_max_entry(e);
+                    if (lane == 0) S.l0[v][(long long)n * Dv.nch + chunk[q]] = rr;
+                    if (rr.key > fmax.key) fmax = rr;
+                }
+            }
+            // frame maximum: untouched chunks from level 0, touched ones recomputed
+            Entry b = fmax;
+#pragma unroll
+            for (int q = 0; q < MAXL0; ++q) {
+                const int cq = lane + 32 * q;
+                bool touched = false;
+                for (int z = 0; z < nr; ++z) touched |= (cq >= lo[z] && cq < hi[z]);
+                if (cq < Dv.nch && !touched && l0v[q].key > b.key) b = l0v[q];
+            }
+            for (int cq = lane + 32 * MAXL0; cq < Dv.nch; cq += 32) {
+                bool touched = false;
+                for (int z = 0; z < nr; ++z) touched |= (cq >= lo[z] && cq < hi[z]);
+                if (touched) continue;
+                const Entry e = l0row[cq];
                 if (e.key > b.key) b = e;
             }
-            Entry r = warp_max_entry(b);
+            const Entry fr = warp_max_entry(b);
             if (lane == 0) {
-                S.l1[v][n] = r;
-                if (S.gshift == 0) {
-                    const int ti = S.tbase[v] + (int)n;
-                    top[ti] = r;
-                    sdirty[ti >> 5] = 1;
-                } else {
-                    tdirty[S.tbase[v] + (int)(n >> S.gshift)] = 1;
-                }
+                S.l1[v][n] = fr;
+                if (S.gshift == 0) top[S.tbase[v] + n] = fr;
+                else tdirty[S.tbase[v] + (n >> S.gshift)] = 1;
             }
         }
         __syncthreads();
@@ -381,57 +468,36 @@ __global__ void __launch_bounds__(LOOP_THREADS, 1)
                 const int i = base + lane;
                 unsigned ball = __ballot_sync(FULL, i < T && tdirty[i]);
                 while (ball) {
-                    const int b = __ffs(ball) - 1;
+                    const int bb = __ffs(ball) - 1;
                     ball &= ball - 1;
-                    const int gi = base + b;
+                    const int gi = base + bb;
                     int w = 0;
                     while (w + 1 < W && S.tbase[w + 1] <= gi) ++w;
-                    const long long f0 = (long long)(gi - S.tbase[w]) << S.gshift;
-                    const long long f1 = min(f0 + (1ll << S.gshift), S.N[w]);
-                    Entry bb;
-                    bb.key = 0;
-                    bb.val = make_float2(0.f, 0.f);
-                    for (long long f = f0 + lane; f < f1; f += 32) {
-                        Entry e = S.l1[w][f];
-                        if (e.key > bb.key) bb = e;
+                    const int f0 = (gi - S.tbase[w]) << S.gshift;
+                    const int f1 = min(f0 + (1 << S.gshift), (int)S.N[w]);
+                    Entry m2;
+                    m2.key = 0;
+                    m2.val = make_float2(0.f, 0.f);
+                    for (int f = f0 + lane; f < f1; f += 32) {
+                        const Entry e = S.l1[w][f];
+                        if (e.key > m2.key) m2 = e;
                     }
-                    Entry r = warp_max_entry(bb);
+                    const Entry gr = warp_max_entry(m2);
                     if (lane == 0) {
-                        S.grp[gi] = r;
-                        top[gi] = r;
+                        S.grp[gi] = gr;
+                        top[gi] = gr;
                         tdirty[gi] = 0;
-                        sdirty[gi >> 5] = 1;
                     }
                 }
             }
             __syncthreads();
         }
-
-        // ---- supers --------------------------------------------------------
-        for (int base = warp * 32; base < NS; base += NWARPS * 32) {
-            const int i = base + lane;
-            unsigned ball = __ballot_sync(FULL, i < NS && sdirty[i]);
-            while (ball) {
-                const int b = __ffs(ball) - 1;
-                ball &= ball - 1;
-                const int s = base + b;
-                const int ti = s * 32 + lane;
-                Entry e;
-                if (ti < T) e = top[ti]; else { e.key = 0; e.val = make_float2(0.f, 0.f); }
-                Entry r = warp_max_entry(e);
-                if (lane == 0) {
-                    sup[s] = r;
-                    sdirty[s] = 0;
-                }
-            }
-        }
-        __syncthreads();
     }
     if (tid == 0) {
         Sg.k = k;
         Sg.E = E;
-        if (sh.stop > 0) {
-            Sg.stop = sh.stop;
+        if (stop > 0) {
+            Sg.stop = stop;
             Sg.timed_out = 0;
         } else {
             Sg.stop = 0;
@@ -440,23 +506,42 @@ __global__ void __launch_bounds__(LOOP_THREADS, 1)
     }
 }
 
+template <int NT>
+cudaError_t launch_nt(const DevPlan& P, DevSig* d_sigs, const int* d_order, int nsig, long long kmax,
+                      double thr_scale, long long budget_ns, size_t smem, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_mp_loop<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_mp_loop<NT><<<nsig, NT, smem, st>>>(P, d_sigs, d_order, kmax, thr_scale, budget_ns);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
-size_t mp_loop_smem_bytes(int T, int) {
-    const int NS = (T + 31) / 32;
-    size_t b = (size_t)(T + NS) * sizeof(Entry) + (size_t)T + (size_t)NS;
+size_t mp_loop_smem_bytes(const DevPlan& P, int T) {
+    size_t b = (size_t)T * sizeof(Entry) + (size_t)P.ncls * sizeof(DevClass) +
+               (size_t)P.ngam * sizeof(float2) + (size_t)T;
     return (b + 15) & ~(size_t)15;
+}
+
+int mp_loop_threads(int nsig, int num_sms) {
+    // one CTA per signal: wide CTAs when the signals leave SMs idle, narrow
+    // ones (several CTAs per SM) when there are more signals than SMs
+    if (nsig <= num_sms / 2) return 1024;
+    if (nsig <= num_sms) return 512;
+    return 256;
 }
 
 cudaError_t launch_mp_loop(const DevPlan& P, DevSig* d_sigs, const int* d_order, int nsig,
                            long long kmax, double thr_scale, long long budget_ns, size_t smem,
-                           cudaStream_t st) {
+                           int threads, cudaStream_t st) {
     if (nsig <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_mp_loop, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    k_mp_loop<<<nsig, LOOP_THREADS, smem, st>>>(P, d_sigs, d_order, kmax, thr_scale, budget_ns);
-    return cudaGetLastError();
+    switch (threads) {
+        case 1024: return launch_nt<1024>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, st);
+        case 512: return launch_nt<512>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, st);
+        case 256: return launch_nt<256>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace mpg

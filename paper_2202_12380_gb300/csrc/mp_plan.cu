@@ -248,6 +248,7 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
     int* d_box = nullptr;
     {
         CK(cudaGetDevice(&p->device));
+        CK(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
         int g_total = 0;
         for (int w = 0; w < W; ++w) {
             p->wlen[w] = win_len[w];
@@ -442,6 +443,8 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
         }
         CK(cudaStreamSynchronize(st));
         p->dp.cls = p->d_cls;
+        p->dp.ncls = (int)p->cls.size();
+        p->dp.ngam = (int)gam_compact.size();
         p->dp.tiles = p->d_tiles;
         p->dp.gam = p->d_gam;
         p->dp.g32 = p->d_g32;
