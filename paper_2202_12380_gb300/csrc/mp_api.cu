@@ -44,7 +44,8 @@ struct mp_state {
     int* d_group_prefix;
     long long total_groups;
     int Tmax;
-    size_t smem;
+    size_t smem;             // MP launch shape (see mp_loop_shape)
+    int threads, cs;
     long long cap;           // atom capacity per signal
     mp_atom* d_atoms;
     double* d_errs;
@@ -244,7 +245,7 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
         state_free(s);
         return cuda_fail(e, "mp_analyze: state set-up");
     }
-    s->smem = mp_loop_smem_bytes(p->dp, s->Tmax);
+    mp_loop_shape(p->dp, s->hs.data(), B, p->num_sms, &s->threads, &s->cs, &s->smem);
     *out = s;
     return MP_OK;
 }
@@ -393,13 +394,8 @@ extern "C" int mp_run_async(mp_state* s, int64_t K_max, double target_snr_db) {
     const double thr_scale = std::pow(10.0, -target_snr_db / 10.0);
     const long long budget =
         s->time_limit_s > 0 ? (long long)std::min(s->time_limit_s * 1e9, 9e18) : 0LL;
-    int threads = mp_loop_threads(s->B, s->plan->num_sms);
-    if (const char* ov = getenv("MPGABOR_LOOP_THREADS")) {  // tuning override: 256, 512 or 1024
-        int t = atoi(ov);
-        if (t == 256 || t == 512 || t == 1024) threads = t;
-    }
     CKR(launch_mp_loop(s->plan->dp, s->d_sigs, s->d_order, s->B, K_max, thr_scale, budget, s->smem,
-                       threads, s->plan->stream));
+                       s->threads, s->cs, s->plan->stream));
     return MP_OK;
 }
 

@@ -103,14 +103,17 @@ cudaError_t launch_group_build(const DevSig* d_sigs, int nsig, const int* d_grou
                                long long total_groups, int W, cudaStream_t st);
 cudaError_t launch_mp_loop(const DevPlan& P, DevSig* d_sigs, const int* d_order, int nsig,
                            long long kmax, double thr_scale, long long budget_ns, size_t smem,
-                           int threads, cudaStream_t st);
+                           int threads, int cs, cudaStream_t st);
+void mp_loop_shape(const DevPlan& P, const DevSig* hs, int B, int num_sms, int* threads, int* cs,
+                   size_t* smem);
 cudaError_t launch_synth(const DevPlan& P, const DevSig* d_sig, long long natoms, float* y,
                          long long L, cudaStream_t st);
 cudaError_t launch_resid_energy(const DevSig* d_sig, const float* y, long long L,
                                 double* d_partials, int nparts, cudaStream_t st);
 
-size_t mp_loop_smem_bytes(const DevPlan& P, int T);
+size_t mp_loop_smem_bytes(const DevPlan& P, int T, int threads, int cs);
 int mp_loop_threads(int nsig, int num_sms);
+int mp_loop_max_clusters(int threads, int cs, size_t smem);
 
 }  // namespace mpg
 

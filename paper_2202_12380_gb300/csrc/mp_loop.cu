@@ -25,7 +25,19 @@
 // Every warp computes the same selection; thread 0 alone writes the atom list
 // and keeps the FP64 energy E, whose stop tests it publishes for the next
 // iteration before the closing barrier.
+//
+// Clusters.  A signal may be given a thread-block cluster of CS CTAs (on CS
+// SMs) instead of one CTA: frame n of every dictionary belongs to CTA
+// n mod CS, which holds its top-level entry and runs its frame jobs.  In step
+// 1 each warp pushes its best candidate into every CTA's shared memory
+// (distributed shared memory) and the cluster barrier replaces the CTA
+// barrier; every CTA then takes the same selection.  The time limit is
+// decided by CTA 0 and pushed the same way, so all CTAs leave the loop in the
+// same iteration.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
+
+#include <cstdlib>
 
 #include "mp_common_dev.cuh"
 #include "mp_internal.cuh"
@@ -158,15 +170,19 @@ __device__ __forceinline__ float2 gamma_of(const DevDict& D, const float2* sgam,
 template <int NT>
 __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
     k_mp_loop(DevPlan P, DevSig* __restrict__ sigs, const int* __restrict__ order,
-              long long kmax, double thr_scale, long long budget_ns) {
+              long long kmax, double thr_scale, long long budget_ns, int CS) {
+    namespace cg = cooperative_groups;
     constexpr int NWARPS = NT / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ DevSig S;
     __shared__ DevDict sd[MAXW];
     __shared__ DevPair sp[MAXW * MAXW];
-    __shared__ Entry wbest[NWARPS];
     __shared__ int sstop[2];  // stop decision per iteration parity
-    DevSig& Sg = sigs[order[blockIdx.x]];
+    __shared__ int cflag[2];  // time-limit decision of CTA 0, per parity
+    __shared__ int ltb[MAXW + 1];  // local top-level base per dictionary
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = CS > 1 ? (int)cluster.block_rank() : 0;
+    DevSig& Sg = sigs[order[blockIdx.x / CS]];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     {
         const int* src = reinterpret_cast<const int*>(&Sg);
@@ -177,8 +193,22 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
     for (int i = tid; i < W; i += NT) sd[i] = P.d[i];
     for (int i = tid; i < W * W; i += NT) sp[i] = P.p[i];
     __syncthreads();
-    const int T = S.T;
-    Entry* top = reinterpret_cast<Entry*>(smem_raw);
+    // top level of this CTA: all frames (CS == 1, with frame groups when
+    // 2^gshift > 1) or the frames n = rank (mod CS) (CS > 1, gshift == 0)
+    if (tid == 0) {
+        int b = 0;
+        for (int w = 0; w < W; ++w) {
+            ltb[w] = b;
+            b += CS > 1 ? (int)(S.N[w] / CS) : S.tbase[w + 1] - S.tbase[w];
+        }
+        ltb[W] = b;
+        cflag[0] = cflag[1] = 0;
+    }
+    __syncthreads();
+    const int T = ltb[W];
+    const int NC = CS * NWARPS;  // candidates exchanged per iteration
+    Entry* cand = reinterpret_cast<Entry*>(smem_raw);           // [2][NC]
+    Entry* top = cand + 2 * NC;
     DevClass* scls = reinterpret_cast<DevClass*>(top + T);
     float2* sgam = reinterpret_cast<float2*>(scls + P.ncls);
     unsigned char* tdirty = reinterpret_cast<unsigned char*>(sgam + P.ngam);
@@ -186,12 +216,16 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
     for (int i = tid; i < P.ncls; i += NT) scls[i] = P.cls[i];
     for (int i = tid; i < P.ngam; i += NT) sgam[i] = P.gam[i];
     for (int w = 0; w < W; ++w) {
-        const int tb = S.tbase[w], te = S.tbase[w + 1];
-        const Entry* src = S.gshift == 0 ? S.l1[w] : S.grp + tb;
-        for (int i = tid; i < te - tb; i += NT) top[tb + i] = src[i];
+        const int tb = ltb[w], te = ltb[w + 1];
+        if (CS > 1) {
+            for (int i = tid; i < te - tb; i += NT) top[tb + i] = S.l1[w][(long long)i * CS + rank];
+        } else {
+            const Entry* src = S.gshift == 0 ? S.l1[w] : S.grp + S.tbase[w];
+            for (int i = tid; i < te - tb; i += NT) top[tb + i] = src[i];
+        }
     }
     for (int i = tid; i < T; i += NT) tdirty[i] = 0;
-    __syncthreads();
+    if (CS > 1) cluster.sync(); else __syncthreads();
 
     long long k = S.k;
     // FP64 work stays in thread 0 (the FP64 pipe is narrow on this part):
@@ -224,14 +258,26 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
                 if (e.key > b.key) b = e;
             }
             const Entry r = warp_max_entry(b);
-            if (lane == 0) wbest[warp] = r;
-            // the time limit is read once per iteration by one thread so that
-            // every warp takes the same decision
-            if (tid == 0 && sstop[k & 1] == 0 && budget_ns > 0 &&
-                (long long)(gtimer() - t_start) > budget_ns)
-                sstop[k & 1] = -1;
+            Entry* slot = cand + (k & 1) * NC + rank * NWARPS + warp;
+            // the time limit is read once per iteration by one thread (of CTA
+            // 0) so that every warp of every CTA takes the same decision
+            int tflag = 0;
+            if (tid == 0 && rank == 0 && budget_ns > 0 && (long long)(gtimer() - t_start) > budget_ns)
+                tflag = 1;
+            if (CS > 1) {
+                if (lane < CS) {
+                    Entry* rs = static_cast<Entry*>(__cluster_map_shared_rank(slot, lane));
+                    *rs = r;
+                }
+                if (tid == 0 && rank == 0)
+                    for (int q = 0; q < CS; ++q)
+                        *static_cast<int*>(__cluster_map_shared_rank(&cflag[k & 1], q)) = tflag;
+            } else {
+                if (lane == 0) *slot = r;
+                if (tid == 0) cflag[k & 1] = tflag;
+            }
         }
-        __syncthreads();
+        if (CS > 1) cluster.sync(); else __syncthreads();
 
         // ---- 2. selection, adjustment, update description (every warp) --
         Entry best;
@@ -239,10 +285,15 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
             Entry b;
             b.key = 0;
             b.val = make_float2(0.f, 0.f);
-            if (lane < NWARPS) b = wbest[lane];
+            const Entry* cb = cand + (k & 1) * NC;
+            for (int i = lane; i < NC; i += 32) {
+                const Entry e = cb[i];
+                if (e.key > b.key) b = e;
+            }
             best = warp_max_entry(b);
         }
         stop = sstop[k & 1];
+        if (stop == 0 && cflag[k & 1]) stop = -1;
         if (stop == 0 && (unsigned)(best.key >> 32) == 0u) stop = MP_STOP_ZEROMAX;
         if (stop) break;
 
@@ -279,6 +330,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
         }
         if (tid == 0) {
             E -= (double)Edf;
+        }
+        if (tid == 0 && rank == 0) {
             mp_atom at;
             at.dict = u;
             at.m = kk;
@@ -287,6 +340,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
             at.im = cy;
             S.atoms[k] = at;
             S.errs[k] = E;
+        }
+        if (tid == 0) {
             int s1 = 0;  // stop tests before the next selection
             if (E <= 0.0) s1 = MP_STOP_NEGENERGY;
             else if (E <= thr) s1 = MP_STOP_SNR;
@@ -326,6 +381,10 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
                     const int nc = hi - lo;
                     if (nc >= Nv) { nstart = 0; nframes = Nv; }
                     else { nstart = imod(lo, Nv); nframes = nc; }
+                    // frames of the hull owned by this CTA: i = i0, i0 + CS, ...
+                    const int i0 = imod(rank - nstart, CS);
+                    nstart += i0;  // first owned frame (may reach N_v: wrapped below)
+                    nframes = nframes > i0 ? (nframes - i0 + CS - 1) / CS : 0;
                 }
             }
         }
@@ -353,7 +412,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
             const Term t1 = shfl_term(mine, 2 * v + 1);
             const DevDict& Dv = sd[v];
             const int Nv = (int)S.N[v];
-            int n = sv + (g - (pv - fv));
+            int n = sv + (g - (pv - fv)) * CS;
             if (n >= Nv) n -= Nv;
             // level-0 entries of the whole frame (untouched chunks keep theirs)
             const Entry* l0row = S.l0[v] + (long long)n * Dv.nch;
@@ -456,14 +515,15 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
             const Entry fr = warp_max_entry(b);
             if (lane == 0) {
                 S.l1[v][n] = fr;
-                if (S.gshift == 0) top[S.tbase[v] + n] = fr;
-                else tdirty[S.tbase[v] + (n >> S.gshift)] = 1;
+                if (CS > 1) top[ltb[v] + n / CS] = fr;
+                else if (S.gshift == 0) top[ltb[v] + n] = fr;
+                else tdirty[ltb[v] + (n >> S.gshift)] = 1;
             }
         }
         __syncthreads();
 
         // ---- level 2 (groups) of touched frames --------------------------
-        if (S.gshift > 0) {
+        if (CS == 1 && S.gshift > 0) {
             for (int base = warp * 32; base < T; base += NWARPS * 32) {
                 const int i = base + lane;
                 unsigned ball = __ballot_sync(FULL, i < T && tdirty[i]);
@@ -493,7 +553,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
             __syncthreads();
         }
     }
-    if (tid == 0) {
+    if (CS > 1) cluster.sync();  // no CTA leaves while others may address it
+    if (tid == 0 && rank == 0) {
         Sg.k = k;
         Sg.E = E;
         if (stop > 0) {
@@ -508,38 +569,132 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
 
 template <int NT>
 cudaError_t launch_nt(const DevPlan& P, DevSig* d_sigs, const int* d_order, int nsig, long long kmax,
-                      double thr_scale, long long budget_ns, size_t smem, cudaStream_t st) {
+                      double thr_scale, long long budget_ns, size_t smem, int cs, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k_mp_loop<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_mp_loop<NT><<<nsig, NT, smem, st>>>(P, d_sigs, d_order, kmax, thr_scale, budget_ns);
+    if (cs > 8) {
+        e = cudaFuncSetAttribute(k_mp_loop<NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nsig * cs));
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_mp_loop<NT>, P, d_sigs, d_order, kmax, thr_scale, budget_ns, cs);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+template <int NT>
+int max_clusters(int cs, size_t smem) {
+    if (cs > 8 &&
+        cudaFuncSetAttribute(k_mp_loop<NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess)
+        return 0;
+    if (cudaFuncSetAttribute(k_mp_loop<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cs);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_mp_loop<NT>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
 }
 
 }  // namespace
 
-size_t mp_loop_smem_bytes(const DevPlan& P, int T) {
-    size_t b = (size_t)T * sizeof(Entry) + (size_t)P.ncls * sizeof(DevClass) +
-               (size_t)P.ngam * sizeof(float2) + (size_t)T;
+size_t mp_loop_smem_bytes(const DevPlan& P, int T, int threads, int cs) {
+    size_t b = (size_t)2 * cs * (threads / 32) * sizeof(Entry) + (size_t)T * sizeof(Entry) +
+               (size_t)P.ncls * sizeof(DevClass) + (size_t)P.ngam * sizeof(float2) + (size_t)T;
     return (b + 15) & ~(size_t)15;
 }
 
+int mp_loop_max_clusters(int threads, int cs, size_t smem) {
+    switch (threads) {
+        case 1024: return max_clusters<1024>(cs, smem);
+        case 512: return max_clusters<512>(cs, smem);
+        case 256: return max_clusters<256>(cs, smem);
+        default: return 0;
+    }
+}
+
 int mp_loop_threads(int nsig, int num_sms) {
-    // one CTA per signal: wide CTAs when the signals leave SMs idle, narrow
-    // ones (several CTAs per SM) when there are more signals than SMs
-    if (nsig <= num_sms / 2) return 1024;
-    if (nsig <= num_sms) return 512;
-    return 256;
+    // 512-thread CTAs while every signal has SMs to itself, 256-thread CTAs
+    // (two per SM) when there are more signals than SMs
+    return nsig <= num_sms ? 512 : 256;
+}
+
+// launch shape for B signals: threads per CTA, cluster size and dynamic
+// shared memory.  Clusters give a signal several SMs while there are SMs to
+// spare; they need every N_w divisible by the cluster size and the per-CTA
+// top level to fit on chip.
+void mp_loop_shape(const DevPlan& P, const DevSig* hs, int B, int num_sms, int* threads, int* cs,
+                   size_t* smem) {
+    int nt = mp_loop_threads(B, num_sms);
+    int c = B <= 8 ? 16 : B <= 16 ? 8 : B * 4 <= num_sms ? 4 : B * 2 <= num_sms ? 2 : 1;
+    if (const char* ov = getenv("MPGABOR_LOOP_THREADS")) {  // tuning overrides
+        int t = atoi(ov);
+        if (t == 256 || t == 512 || t == 1024) nt = t;
+    }
+    if (const char* ov = getenv("MPGABOR_CLUSTER")) {
+        int t = atoi(ov);
+        if (t == 1 || t == 2 || t == 4 || t == 8 || t == 16) c = t;
+    }
+    for (; c > 1; c >>= 1) {
+        bool ok = true;
+        int lt = 0;
+        for (int b = 0; b < B && ok; ++b) {
+            int t = 0;
+            for (int w = 0; w < P.W; ++w) {
+                if (hs[b].N[w] % c) ok = false;
+                t += (int)(hs[b].N[w] / c);
+            }
+            lt = t > lt ? t : lt;
+        }
+        if (!ok || lt > TOPCAP) continue;
+        const size_t sm = mp_loop_smem_bytes(P, lt, nt, c);
+        if (mp_loop_max_clusters(nt, c, sm) < 1) continue;
+        *threads = nt;
+        *cs = c;
+        *smem = sm;
+        return;
+    }
+    int tmax = 1;
+    for (int b = 0; b < B; ++b) tmax = hs[b].T > tmax ? hs[b].T : tmax;
+    *threads = nt;
+    *cs = 1;
+    *smem = mp_loop_smem_bytes(P, tmax, nt, 1);
 }
 
 cudaError_t launch_mp_loop(const DevPlan& P, DevSig* d_sigs, const int* d_order, int nsig,
                            long long kmax, double thr_scale, long long budget_ns, size_t smem,
-                           int threads, cudaStream_t st) {
+                           int threads, int cs, cudaStream_t st) {
     if (nsig <= 0) return cudaSuccess;
     switch (threads) {
-        case 1024: return launch_nt<1024>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, st);
-        case 512: return launch_nt<512>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, st);
-        case 256: return launch_nt<256>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, st);
+        case 1024: return launch_nt<1024>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, cs, st);
+        case 512: return launch_nt<512>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, cs, st);
+        case 256: return launch_nt<256>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, cs, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -235,8 +235,10 @@ extern "C" int mp_decompose_static(const mp_plan* p, const float* x_dev, int64_t
     }
     CKS(launch_group_build(d_sig, 1, d_gp, t.group_prefix[1], W, st));
     const double thr_scale = std::pow(10.0, -target_snr_db / 10.0);
-    CKS(launch_mp_loop(p->dp, d_sig, d_order, 1, K_max, thr_scale, 0, mp_loop_smem_bytes(p->dp, tb),
-                       mp_loop_threads(1, p->num_sms), st));
+    int threads = 0, cs = 1;
+    size_t smem = 0;
+    mp_loop_shape(p->dp, &S, 1, p->num_sms, &threads, &cs, &smem);
+    CKS(launch_mp_loop(p->dp, d_sig, d_order, 1, K_max, thr_scale, 0, smem, threads, cs, st));
     if (n_atoms || stop_reason || final_snr_db) {
         DevSig out;
         CKS(cudaMemcpyAsync(&out, d_sig, sizeof(DevSig), cudaMemcpyDeviceToHost, st));

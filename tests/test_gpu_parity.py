@@ -279,3 +279,32 @@ def test_analyze_host_matches_device():
     st_h = mg.mp_analyze_host(plan, [x])
     mg.mp_run(st_h, 200, 200.0)
     assert np.array_equal(mg.mp_get_atoms(st, 0), mg.mp_get_atoms(st_h, 0))
+
+
+@pytest.mark.parametrize("cluster", ["1", "4", "16"])
+@pytest.mark.parametrize("kind", ["multi3", "mixed"])
+def test_mp_parity_launch_shapes(kind, cluster, monkeypatch):
+    """The same decomposition with one CTA per signal and with clusters of 4
+    and 16 CTAs (frames interleaved across the cluster's SMs)."""
+    monkeypatch.setenv("MPGABOR_CLUSTER", cluster)
+    L, dicts = _workload_small(kind)
+    x = inputs.as_f32(inputs.mixture(L, 33, fs=16000.0))
+    K = 300
+    ref = cmp.mp_coef(dicts, x.astype(np.float64), 1e-4, K, 200.0)
+    _, _, out = _run_gpu(dicts, [x], 1e-4, K, 200.0)
+    atoms, errs, E0, stop = out[0]
+    assert atoms.size == K
+    compare(atoms, errs, E0, ref, min_checked=100)
+
+
+def test_many_signals_narrow_ctas():
+    """More signals than SMs: 256-thread CTAs, two per SM, each signal
+    checked against its own oracle run."""
+    dicts = [(inputs.blackman(64), 16, 64), (inputs.hann(128), 32, 128)]
+    B = 200
+    xs = [inputs.as_f32(inputs.mixture(1024, 1000 + i, fs=8000.0)) for i in range(B)]
+    K = 40
+    _, _, out = _run_gpu(dicts, xs, 1e-4, K, 200.0)
+    for i, (x, (atoms, errs, E0, stop)) in enumerate(zip(xs, out)):
+        ref = cmp.mp_coef(dicts, x.astype(np.float64), 1e-4, K, 200.0)
+        compare(atoms, errs, E0, ref, min_checked=10)
