@@ -157,7 +157,7 @@ __global__ void k_tree_build(DevPlan P, const DevSig* __restrict__ sigs, int nsi
     const DevDict& D = P.d[dict];
     const float2* row = S.plane[dict] + n * D.Mrp;
     Entry* l0 = S.l0[dict] + n * D.nch;
-    const unsigned fb = S.fbase[dict] + (unsigned)(n * D.Mr);
+    const unsigned fb = S.fbase[dict] + ((unsigned)n << D.msh);
     Entry best;
     best.key = 0;
     best.val = make_float2(0.f, 0.f);

@@ -106,9 +106,11 @@ int validate_lengths(const mp_plan* p, int B, const int64_t* L) {
             return MP_EINVAL;
         }
         unsigned long long P = 0;
-        for (int w = 0; w < p->W; ++w) P += (unsigned long long)(L[b] / p->a[w]) * (p->M[w] / 2 + 1);
+        for (int w = 0; w < p->W; ++w)
+            P += (unsigned long long)(L[b] / p->a[w]) << p->dp.d[w].msh;
         if (P >= 0xffffffffull) {
-            mpg_set_error("mp_analyze: signal %d has %llu coefficients (limit 2^32-1)", b, P);
+            mpg_set_error("mp_analyze: signal %d needs a flat index range of %llu (limit 2^32-1)",
+                          b, P);
             return MP_EINVAL;
         }
     }
@@ -148,8 +150,9 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
         for (int w = 0; w < W; ++w) {
             const DevDict& D = p->dp.d[w];
             S.N[w] = L[b] / D.a;
+            S.Nmask[w] = (S.N[w] & (S.N[w] - 1)) == 0 ? (int)(S.N[w] - 1) : 0;
             S.fbase[w] = fb;
-            fb += (unsigned)(S.N[w] * D.Mr);
+            fb += (unsigned)(S.N[w] << D.msh);
             F += S.N[w];
             o_plane[b * W + w] = off;
             off = align256(off + sizeof(float2) * S.N[w] * D.Mrp);

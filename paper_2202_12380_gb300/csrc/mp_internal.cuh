@@ -11,7 +11,7 @@
 //             dictionary
 // An Entry packs the selection key and the coefficient it belongs to:
 //   key = (float bits of |rho|^2) << 32 | (0xffffffff - flat index),
-//   flat = fbase[w] + n * (M_w/2 + 1) + m,
+//   flat = fbase[w] + n * 2^msh_w + m   (2^msh_w >= M_w/2 + 1),
 // so an unsigned max over keys is the argmax of |rho|^2 with ties broken
 // towards the lowest (w, n, m).  |rho|^2 >= 0, so its float bits order like
 // the values.
@@ -38,11 +38,16 @@ struct DevDict {
     int wlen, a, M, Mr, nch, Mrp;  // Mr = M/2+1 stored bins, Mrp padded to CHUNK
     int gam_lo, gam_hi, gam_off;   // compact <d, conj d> table (see mp_plan.cu)
     int g_off;                     // offset of the FP32 window in DevPlan::g32
+    int msh;                       // flat-index row stride 2^msh >= Mr
+    int Mmask;                     // M - 1 if M is a power of two, else 0
 };
 
 struct DevPair {
     int rf, rt;      // alignment classes in frequency / time
     int cls_base;    // first class descriptor of the pair
+    int rf_sh, rt_sh;  // log2(rf), log2(rt), or -1 if not a power of two
+    int mratio;      // M_v / M_u when M_v >= M_u, else 0
+    int aratio;      // a_u / a_v when a_v <= a_u, else 0
     int pad;
 };
 
@@ -69,6 +74,7 @@ struct DevPlan {
 struct DevSig {
     long long L;
     long long N[MAXW];
+    int Nmask[MAXW];  // N_w - 1 if N_w is a power of two, else 0
     unsigned fbase[MAXW + 1];
     int tbase[MAXW + 1];
     float2* plane[MAXW];

@@ -104,13 +104,15 @@ __device__ __forceinline__ Term make_term(const DevDict* sd, const DevPair* sp,
     const DevPair& PR = sp[u * W + v];
     const int Mu = Du.M, Mv = Dv.M, au = Du.a, av = Dv.a;
     const int kk = t == 0 ? k : Mu - k;
-    const int ct = j % PR.rt;
-    const int cf = kk % PR.rf;
+    const int ct = PR.rt_sh >= 0 ? (j & (PR.rt - 1)) : j % PR.rt;
+    const int cf = PR.rf_sh >= 0 ? (kk & (PR.rf - 1)) : kk % PR.rf;
     const DevClass& C = scls[PR.cls_base + cf * PR.rt + ct];
     if (C.R == 0) return T;
-    const int base_m = (Mv >= Mu) ? kk * (Mv / Mu) : (kk - cf) / PR.rf;
-    const int base_n = (av <= au) ? j * (au / av) : (j - ct) / PR.rt;
-    T.Arow = imod(base_m + C.i_lo, Mv);
+    const int base_m = PR.mratio ? kk * PR.mratio
+                                 : (PR.rf_sh >= 0 ? (kk - cf) >> PR.rf_sh : (kk - cf) / PR.rf);
+    const int base_n = PR.aratio ? j * PR.aratio
+                                 : (PR.rt_sh >= 0 ? (j - ct) >> PR.rt_sh : (j - ct) / PR.rt);
+    T.Arow = Dv.Mmask ? ((base_m + C.i_lo) & Dv.Mmask) : imod(base_m + C.i_lo, Mv);
     T.R = C.R;
     // any stored row (0 .. M_v/2) inside [Arow, Arow + R) mod M_v ?
     const bool rows = (T.Arow < Dv.Mr) || (T.Arow + T.R > Mv);
@@ -120,7 +122,7 @@ __device__ __forceinline__ Term make_term(const DevDict* sd, const DevPair* sp,
     T.kk = kk;
     T.tau0 = C.c_lo * av - ct * au;
     T.a0 = base_n + C.c_lo;
-    T.Acol = imod(T.a0, (int)S.N[v]);
+    T.Acol = S.Nmask[v] ? (T.a0 & S.Nmask[v]) : imod(T.a0, (int)S.N[v]);
     T.tile = C.off;
     return T;
 }
@@ -150,12 +152,18 @@ __device__ __forceinline__ bool term_hit(const Term& T, int m, int n, int Mv, in
     return true;
 }
 
-__device__ __forceinline__ float2 term_phase(const Term& T, int n, int Nv, int av, int Mu) {
+__device__ __forceinline__ float2 term_phase(const Term& T, int n, int Nv, int av, int Mu,
+                                             int Mumask) {
     int cc = n - T.Acol;
     if (cc < 0) cc += Nv;
     const int tau = T.tau0 + cc * av;
-    const unsigned tm = (unsigned)imod(tau, Mu);
-    const unsigned q = ((unsigned)T.kk * tm) % (unsigned)Mu;
+    unsigned q;
+    if (Mumask) {
+        q = ((unsigned)T.kk * ((unsigned)tau & (unsigned)Mumask)) & (unsigned)Mumask;
+    } else {
+        const unsigned tm = (unsigned)imod(tau, Mu);
+        q = ((unsigned)T.kk * tm) % (unsigned)Mu;
+    }
     float sn, cs;
     sincospif(2.0f * (float)q / (float)Mu, &sn, &cs);
     return make_float2(cs, sn);
@@ -168,7 +176,7 @@ __device__ __forceinline__ float2 gamma_of(const DevDict& D, const float2* sgam,
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     k_mp_loop(DevPlan P, DevSig* __restrict__ sigs, const int* __restrict__ order,
               long long kmax, double thr_scale, long long budget_ns, int CS) {
     namespace cg = cooperative_groups;
@@ -237,7 +245,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
     const unsigned long long t_start = gtimer();
     const float2* __restrict__ tiles = P.tiles;
     int stop = 0;
-    if (tid == 0) {
+    if (tid == NT - 32) {
         int s0 = 0;
         if (!isfinite(E0)) s0 = MP_STOP_INVALID;
         else if (E <= 0.0) s0 = MP_STOP_NEGENERGY;
@@ -261,20 +269,23 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
             Entry* slot = cand + (k & 1) * NC + rank * NWARPS + warp;
             // the time limit is read once per iteration by one thread (of CTA
             // 0) so that every warp of every CTA takes the same decision
-            int tflag = 0;
-            if (tid == 0 && rank == 0 && budget_ns > 0 && (long long)(gtimer() - t_start) > budget_ns)
-                tflag = 1;
             if (CS > 1) {
                 if (lane < CS) {
                     Entry* rs = static_cast<Entry*>(__cluster_map_shared_rank(slot, lane));
                     *rs = r;
                 }
-                if (tid == 0 && rank == 0)
-                    for (int q = 0; q < CS; ++q)
-                        *static_cast<int*>(__cluster_map_shared_rank(&cflag[k & 1], q)) = tflag;
-            } else {
-                if (lane == 0) *slot = r;
-                if (tid == 0) cflag[k & 1] = tflag;
+            } else if (lane == 0) {
+                *slot = r;
+            }
+            if (budget_ns > 0 && rank == 0 && warp == 0) {
+                int tflag = 0;
+                if (lane == 0) tflag = (long long)(gtimer() - t_start) > budget_ns ? 1 : 0;
+                tflag = __shfl_sync(FULL, tflag, 0);
+                if (lane < CS) {
+                    int* rf = CS > 1 ? static_cast<int*>(__cluster_map_shared_rank(&cflag[k & 1], lane))
+                                     : &cflag[k & 1];
+                    *rf = tflag;
+                }
             }
         }
         if (CS > 1) cluster.sync(); else __syncthreads();
@@ -300,11 +311,11 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
         const unsigned flat = 0xffffffffu - (unsigned)(best.key & 0xffffffffull);
         int u = 0;
         while (u + 1 < W && S.fbase[u + 1] <= flat) ++u;
-        const int Mr_u = sd[u].Mr;
         const unsigned rel = flat - S.fbase[u];
-        const int j = (int)(rel / (unsigned)Mr_u);
-        const int kk = (int)(rel - (unsigned)j * (unsigned)Mr_u);
+        const int j = (int)(rel >> sd[u].msh);
+        const int kk = (int)(rel & ((1u << sd[u].msh) - 1u));
         const int Mu = sd[u].M;
+        const int Mumask = sd[u].Mmask;
         const bool edge = (kk == 0) || (2 * kk == Mu);
         // eqs. dualatprod / projenfaster: coefficient and energy drop in FP32
         // (gamma is zero away from m = 0 and m = M/2), E accumulated in FP64
@@ -328,10 +339,13 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
                 Edf = 2.f * (c2 + fmaf(g.x, d2, -2.f * g.y * cx * cy));
             }
         }
-        if (tid == 0) {
+        // bookkeeping (FP64 energy, atom list, next stop decision) in lane 0 of
+        // the last warp, which the frame jobs reach last
+        const bool keeper = (tid == NT - 32);
+        if (keeper) {
             E -= (double)Edf;
         }
-        if (tid == 0 && rank == 0) {
+        if (keeper && rank == 0) {
             mp_atom at;
             at.dict = u;
             at.m = kk;
@@ -341,7 +355,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
             S.atoms[k] = at;
             S.errs[k] = E;
         }
-        if (tid == 0) {
+        if (keeper) {
             int s1 = 0;  // stop tests before the next selection
             if (E <= 0.0) s1 = MP_STOP_NEGENERGY;
             else if (E <= thr) s1 = MP_STOP_SNR;
@@ -429,9 +443,9 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
             const int nr = nr0 + nr1;
             float2* prow = S.plane[v] + (long long)n * Dv.Mrp;
             const float2 w0 =
-                t0.active ? cmul(c_main, term_phase(t0, n, Nv, Dv.a, Mu)) : make_float2(0.f, 0.f);
+                t0.active ? cmul(c_main, term_phase(t0, n, Nv, Dv.a, Mu, Mumask)) : make_float2(0.f, 0.f);
             const float2 w1 =
-                t1.active ? cmul(c_conj, term_phase(t1, n, Nv, Dv.a, Mu)) : make_float2(0.f, 0.f);
+                t1.active ? cmul(c_conj, term_phase(t1, n, Nv, Dv.a, Mu, Mumask)) : make_float2(0.f, 0.f);
             Entry fmax;
             fmax.key = 0;
             fmax.val = make_float2(0.f, 0.f);
@@ -490,7 +504,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
                     if (hit0[q] || hit1[q]) prow[m] = x2;
                     Entry e;
                     e.val = x2;
-                    e.key = (m < Dv.Mr) ? make_key(x2, S.fbase[v] + (unsigned)n * Dv.Mr + m) : 0ull;
+                    e.key = (m < Dv.Mr) ? make_key(x2, S.fbase[v] + ((unsigned)n << Dv.msh) + m) : 0ull;
                     const Entry rr = warp_max_entry(e);
                     if (lane == 0) S.l0[v][(long long)n * Dv.nch + chunk[q]] = rr;
                     if (rr.key > fmax.key) fmax = rr;
@@ -554,7 +568,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1)
         }
     }
     if (CS > 1) cluster.sync();  // no CTA leaves while others may address it
-    if (tid == 0 && rank == 0) {
+    if (tid == NT - 32 && rank == 0) {
         Sg.k = k;
         Sg.E = E;
         if (stop > 0) {
@@ -635,6 +649,7 @@ int mp_loop_max_clusters(int threads, int cs, size_t smem) {
         case 1024: return max_clusters<1024>(cs, smem);
         case 512: return max_clusters<512>(cs, smem);
         case 256: return max_clusters<256>(cs, smem);
+        case 128: return max_clusters<128>(cs, smem);
         default: return 0;
     }
 }
@@ -653,15 +668,20 @@ void mp_loop_shape(const DevPlan& P, const DevSig* hs, int B, int num_sms, int* 
                    size_t* smem) {
     int nt = mp_loop_threads(B, num_sms);
     int c = B <= 8 ? 16 : B <= 16 ? 8 : B * 4 <= num_sms ? 4 : B * 2 <= num_sms ? 2 : 1;
+    int nt_override = 0;
     if (const char* ov = getenv("MPGABOR_LOOP_THREADS")) {  // tuning overrides
         int t = atoi(ov);
-        if (t == 256 || t == 512 || t == 1024) nt = t;
+        if (t == 128 || t == 256 || t == 512 || t == 1024) nt_override = t;
     }
     if (const char* ov = getenv("MPGABOR_CLUSTER")) {
         int t = atoi(ov);
         if (t == 1 || t == 2 || t == 4 || t == 8 || t == 16) c = t;
     }
+    if (nt_override) nt = nt_override;
     for (; c > 1; c >>= 1) {
+        // a cluster CTA runs only a few frame jobs per iteration: one warp per
+        // scheduler keeps the redundant selection off each other's issue slots
+        if (!nt_override) nt = 128;
         bool ok = true;
         int lt = 0;
         for (int b = 0; b < B && ok; ++b) {
@@ -682,7 +702,7 @@ void mp_loop_shape(const DevPlan& P, const DevSig* hs, int B, int num_sms, int* 
     }
     int tmax = 1;
     for (int b = 0; b < B; ++b) tmax = hs[b].T > tmax ? hs[b].T : tmax;
-    *threads = nt;
+    *threads = nt_override ? nt_override : mp_loop_threads(B, num_sms);
     *cs = 1;
     *smem = mp_loop_smem_bytes(P, tmax, nt, 1);
 }
@@ -695,6 +715,7 @@ cudaError_t launch_mp_loop(const DevPlan& P, DevSig* d_sigs, const int* d_order,
         case 1024: return launch_nt<1024>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, cs, st);
         case 512: return launch_nt<512>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, cs, st);
         case 256: return launch_nt<256>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, cs, st);
+        case 128: return launch_nt<128>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, cs, st);
         default: return cudaErrorInvalidValue;
     }
 }

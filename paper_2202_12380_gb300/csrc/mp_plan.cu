@@ -261,6 +261,9 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
             D.Mr = M[w] / 2 + 1;
             D.nch = (D.Mr + CHUNK - 1) / CHUNK;
             D.Mrp = D.nch * CHUNK;
+            D.msh = 0;
+            while ((1 << D.msh) < D.Mr) ++D.msh;
+            D.Mmask = (M[w] & (M[w] - 1)) == 0 ? M[w] - 1 : 0;
             D.g_off = g_total;
             g_total += win_len[w];
             CK(cudaMalloc(&d_win[w], sizeof(double) * win_len[w]));
@@ -320,6 +323,14 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
                 PR.rf = (M[u] > M[v]) ? M[u] / M[v] : 1;
                 PR.rt = (a[v] > a[u]) ? a[v] / a[u] : 1;
                 PR.cls_base = (int)p->cls.size();
+                PR.rf_sh = -1;
+                PR.rt_sh = -1;
+                for (int b = 0; b < 31; ++b) {
+                    if ((1 << b) == PR.rf) PR.rf_sh = b;
+                    if ((1 << b) == PR.rt) PR.rt_sh = b;
+                }
+                PR.mratio = M[v] >= M[u] ? M[v] / M[u] : 0;
+                PR.aratio = a[v] <= a[u] ? a[u] / a[v] : 0;
                 int Mx = p->Mx[pi], an = p->an[pi], tmin = p->tmin[pi], ntau = p->ntau[pi];
                 int tmax = tmin + (ntau - 1) * an;
                 for (int cf = 0; cf < PR.rf; ++cf)

@@ -148,8 +148,9 @@ extern "C" int mp_decompose_static(const mp_plan* p, const float* x_dev, int64_t
     for (int w = 0; w < W; ++w) {
         const DevDict& D = p->dp.d[w];
         S.N[w] = L / D.a;
+        S.Nmask[w] = (S.N[w] & (S.N[w] - 1)) == 0 ? (int)(S.N[w] - 1) : 0;
         S.fbase[w] = (unsigned)P;
-        P += (unsigned long long)S.N[w] * D.Mr;
+        P += (unsigned long long)S.N[w] << D.msh;
         F += S.N[w];
         lay.o_plane[w] = off;
         off = al(off + sizeof(float2) * S.N[w] * D.Mrp);
