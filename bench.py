@@ -212,8 +212,9 @@ def run_gpu(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     cfg, dicts, xs = _workload(args.workload)
     stream = torch.cuda.Stream()
+    aflag = mg.MP_ANALYSIS_BF16X3 if args.analysis == "bf16x3" else mg.MP_ANALYSIS_FP32
     plan = mg.mp_plan_create([d[0] for d in dicts], [d[1] for d in dicts], [d[2] for d in dicts],
-                             cfg["eps"], mg.MP_ANALYSIS_FP32, stream)
+                             cfg["eps"], aflag, stream)
     xd = [torch.from_numpy(x).cuda() for x in xs]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     K, snr = cfg["kmax"], cfg["snr_db"]
@@ -327,7 +328,7 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seeded mixture; the paper's audio is not available)",
-        "config": dict(_config_desc(args.workload, cfg, xs),
+        "config": dict(_config_desc(args.workload, cfg, xs), analysis=args.analysis,
                        parallelism="replicas" if ws > 1 else "single"),
         "atoms_per_step": atoms_per_step,
         "stop_reasons": [int(s) for s in stops[:8]],
@@ -359,8 +360,9 @@ def run_batched(args, mg, torch):
     """Secondary figure: the batched form (256 uneven signals, one launch)."""
     cfg, dicts, xs = _workload("batch256")
     stream = torch.cuda.Stream()
+    aflag = mg.MP_ANALYSIS_BF16X3 if args.analysis == "bf16x3" else mg.MP_ANALYSIS_FP32
     plan = mg.mp_plan_create([d[0] for d in dicts], [d[1] for d in dicts], [d[2] for d in dicts],
-                             cfg["eps"], mg.MP_ANALYSIS_FP32, stream)
+                             cfg["eps"], aflag, stream)
     xd = [torch.from_numpy(x).cuda() for x in xs]
     state = None
     res = []
@@ -381,7 +383,7 @@ def run_batched(args, mg, torch):
     step = float(np.mean([r[0] for r in res]))
     loop = float(np.mean([r[2] for r in res]))
     peak, _ = _peaks()
-    out = {"workload": "batch256", "signals": len(xs), "L_total": int(sum(len(x) for x in xs)),
+    out = {"workload": "batch256", "analysis": args.analysis, "signals": len(xs), "L_total": int(sum(len(x) for x in xs)),
            "atoms_per_step": int(n.sum()), "ms_per_step": step,
            "analysis_ms": float(np.mean([r[1] for r in res])), "mp_loop_ms": loop,
            "value": float(n.sum()) / (step / 1e3), "unit": UNIT,
@@ -455,7 +457,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="multi3_2p18",
-                    choices=["multi3_2p18", "single_gauss_16k", "multi5_2p20"])
+                    choices=["multi3_2p18", "single_gauss_16k", "multi5_2p20", "stress_2p23"])
+    ap.add_argument("--analysis", default="fp32", choices=["fp32", "bf16x3"],
+                    help="analysis precision (bf16x3: split-BF16 DFT-GEMM on tcgen05)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--batched-steps", type=int, default=3)

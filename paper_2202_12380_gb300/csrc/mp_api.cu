@@ -51,6 +51,16 @@ struct mp_state {
     double* d_errs;
     double* d_scalar;
     double time_limit_s;
+    // split-BF16 analysis: padded BF16 signal segments and per-dictionary views
+    void* d_xhi;
+    void* d_xlo;
+    long long* d_seg;        // [2][B]: segment offsets, lengths (elements)
+    int seg_pad;
+    int* d_brow;             // [W][B]: first view row of each signal's frame 0
+    long long* d_tc_prefix[MAXW];
+    long long total_tc_tiles[MAXW];
+    int* d_err;
+    alignas(64) unsigned char tmB[MAXW][2][128];
 };
 
 namespace {
@@ -79,6 +89,13 @@ void state_free(mp_state* s) {
     if (s->d_atoms) cudaFree(s->d_atoms);
     if (s->d_errs) cudaFree(s->d_errs);
     if (s->d_scalar) cudaFree(s->d_scalar);
+    if (s->d_xhi) cudaFree(s->d_xhi);
+    if (s->d_xlo) cudaFree(s->d_xlo);
+    if (s->d_seg) cudaFree(s->d_seg);
+    if (s->d_brow) cudaFree(s->d_brow);
+    for (int w = 0; w < MAXW; ++w)
+        if (s->d_tc_prefix[w]) cudaFree(s->d_tc_prefix[w]);
+    if (s->d_err) cudaFree(s->d_err);
     delete s;
 }
 
@@ -121,6 +138,11 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
     mp_state* s = new mp_state();
+    s->d_xhi = s->d_xlo = nullptr;
+    s->d_seg = nullptr;
+    s->d_brow = nullptr;
+    s->d_err = nullptr;
+    memset(s->d_tc_prefix, 0, sizeof(s->d_tc_prefix));
     memset(s->d_tile_prefix, 0, sizeof(s->d_tile_prefix));
     memset(s->d_frame_prefix, 0, sizeof(s->d_frame_prefix));
     s->plan = p;
@@ -244,6 +266,59 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
     if (e == cudaSuccess) e = cudaMalloc(&s->d_scalar, sizeof(double) * 4);
+    if (e == cudaSuccess && (p->flags & MP_ANALYSIS_BF16X3)) {
+        // padded BF16 segments: seg[j] = x(j - pad), offsets multiples of a_max
+        int amax = 0, wmax = 0, kmax64 = 0;
+        for (int w = 0; w < W; ++w) {
+            amax = std::max(amax, p->a[w]);
+            wmax = std::max(wmax, p->wlen[w]);
+            kmax64 = std::max(kmax64, p->Kp64[w]);
+        }
+        const long long pad = ((wmax / 2 + amax - 1) / amax) * (long long)amax;
+        s->seg_pad = (int)pad;
+        std::vector<long long> seg(2 * B);
+        long long tot = 0;
+        for (int b = 0; b < B; ++b) {
+            const long long len = ((pad + L[b] + kmax64 + amax + amax - 1) / amax) * amax;
+            seg[b] = tot;
+            seg[B + b] = len;
+            tot += len;
+        }
+        std::vector<int> brow((size_t)W * B);
+        for (int w = 0; w < W; ++w)
+            for (int b = 0; b < B; ++b)
+                brow[(size_t)w * B + b] = (int)((seg[b] + pad - p->wlen[w] / 2) / p->a[w]);
+        e = cudaMalloc(&s->d_xhi, 2 * tot);
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_xlo, 2 * tot);
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_seg, sizeof(long long) * 2 * B);
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_brow, sizeof(int) * W * B);
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->d_err, 0, sizeof(int), st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s->d_seg, seg.data(), sizeof(long long) * 2 * B,
+                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s->d_brow, brow.data(), sizeof(int) * W * B, cudaMemcpyHostToDevice,
+                                st);
+        for (int w = 0; w < W && e == cudaSuccess; ++w) {
+            std::vector<long long> tp(B + 1, 0);
+            for (int b = 0; b < B; ++b) tp[b + 1] = tp[b] + (s->hs[b].N[w] + 127) / 128;
+            s->total_tc_tiles[w] = tp[B];
+            e = cudaMalloc(&s->d_tc_prefix[w], sizeof(long long) * (B + 1));
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(s->d_tc_prefix[w], tp.data(), sizeof(long long) * (B + 1),
+                                    cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            const unsigned long long aw = (unsigned long long)p->a[w];
+            if (e == cudaSuccess &&
+                (!encode_bf16_map(s->tmB[w][0], s->d_xhi, aw, tot / aw, aw * 2) ||
+                 !encode_bf16_map(s->tmB[w][1], s->d_xlo, aw, tot / aw, aw * 2))) {
+                state_free(s);
+                return MP_ECUDA;
+            }
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
     if (e != cudaSuccess) {
         state_free(s);
         return cuda_fail(e, "mp_analyze: state set-up");
@@ -282,13 +357,38 @@ int analyze_impl(const mp_plan* p, mp_state** state, int B, const float* const* 
     for (int b = 0; b < B; ++b)
         CKR(cudaMemcpyAsync((void*)s->hs[b].x, x[b], sizeof(float) * L[b], kind, st));
     CKR(launch_energy(s->d_sigs, B, nullptr, 0, st));
+    const bool tc = (p->flags & MP_ANALYSIS_BF16X3) != 0;
+    if (tc)
+        CKR(launch_split_segments(s->d_sigs, B, s->d_seg, s->d_seg + B, s->seg_pad, s->d_xhi,
+                                  s->d_xlo, st));
     for (int w = 0; w < p->W; ++w) {
         const DevDict& D = p->dp.d[w];
-        CKR(launch_analysis_sgemm(p->d_A[w], p->Arows[w], p->Akp[w], D.wlen, D.a, D.Mrp, B,
-                                  s->d_tile_prefix[w], s->d_sigs, w, s->total_tiles[w], st));
+        if (tc) {
+            alignas(64) unsigned char maps[4][128];
+            memcpy(maps[0], p->tmA[w][0], 128);
+            memcpy(maps[1], p->tmA[w][1], 128);
+            memcpy(maps[2], s->tmB[w][0], 128);
+            memcpy(maps[3], s->tmB[w][1], 128);
+            CKR(launch_analysis_tc(maps, p->Arows[w], p->Kp64[w], D.a, D.Mrp, B, s->d_tc_prefix[w],
+                                   s->d_brow + (size_t)w * B, s->d_sigs, w, s->total_tc_tiles[w],
+                                   s->d_err, st));
+        } else {
+            CKR(launch_analysis_sgemm(p->d_A[w], p->Arows[w], p->Akp[w], D.wlen, D.a, D.Mrp, B,
+                                      s->d_tile_prefix[w], s->d_sigs, w, s->total_tiles[w], st));
+        }
         CKR(launch_tree_build(p->dp, s->d_sigs, B, s->d_frame_prefix[w], s->total_frames[w], w, st));
     }
     CKR(launch_group_build(s->d_sigs, B, s->d_group_prefix, s->total_groups, p->W, st));
+    if (tc) {
+        // the tensor-core kernel bounds its waits; report an expired wait
+        int err = 0;
+        CKR(cudaMemcpyAsync(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CKR(cudaStreamSynchronize(st));
+        if (err) {
+            mpg_set_error("mp_analyze: a tensor-core analysis wait timed out");
+            return MP_ETIMEOUT;
+        }
+    }
     if (kind == cudaMemcpyHostToDevice) CKR(cudaStreamSynchronize(st));
     *state = s;
     return MP_OK;

@@ -117,6 +117,22 @@ cudaError_t launch_synth(const DevPlan& P, const DevSig* d_sig, long long natoms
 cudaError_t launch_resid_energy(const DevSig* d_sig, const float* y, long long L,
                                 double* d_partials, int nparts, cudaStream_t st);
 
+// tensor-core (split-BF16) analysis, mp_analysis_tc.cu
+int analysis_tc_smem();
+cudaError_t launch_split_rows(const float* src, int rows, int cols, int src_ld, int cols_p,
+                              void* hi, void* lo, cudaStream_t st);
+cudaError_t launch_split_segments(const DevSig* d_sigs, int nsig, const long long* seg_off,
+                                  const long long* seg_len, int pad, void* hi, void* lo,
+                                  cudaStream_t st);
+cudaError_t launch_analysis_tc(const void* tmaps, int Arows, int Kp, int a, int Mrp, int nsig,
+                               const long long* d_tile_prefix, const int* d_brow,
+                               const DevSig* d_sigs, int dict, long long total_tiles, int* d_err,
+                               cudaStream_t st);
+// encodes a 2-D BF16 tensor map with a 64 x 128 box and 128-byte swizzle
+// (mp_plan.cu); returns false on failure
+bool encode_bf16_map(void* map, const void* base, unsigned long long inner,
+                     unsigned long long outer, unsigned long long row_bytes);
+
 size_t mp_loop_smem_bytes(const DevPlan& P, int T, int threads, int cs);
 int mp_loop_threads(int nsig, int num_sms);
 int mp_loop_max_clusters(int threads, int cs, size_t smem);
@@ -153,5 +169,10 @@ struct mp_plan {
     float* d_g32;
     float* d_A[mpg::MAXW];  // FP32 DFT matrices for the analysis, [Arows][Akp]
     int Arows[mpg::MAXW], Akp[mpg::MAXW];
+    // split-BF16 analysis (MP_ANALYSIS_BF16X3): A = A_hi + A_lo, [Arows][Kp64]
+    void* d_Ahi[mpg::MAXW];
+    void* d_Alo[mpg::MAXW];
+    int Kp64[mpg::MAXW];
+    alignas(64) unsigned char tmA[mpg::MAXW][2][128];  // CUtensorMap of A_hi, A_lo
 };
 #endif

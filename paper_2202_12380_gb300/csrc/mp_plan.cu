@@ -15,6 +15,7 @@
 // its own dense tile over the bounding box of the entries with |h| > eps
 // (entries at or below eps inside the box are stored as 0), so the update of
 // dictionary v is a dense rectangle of its coefficient plane.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,6 +25,8 @@
 #include <vector>
 
 #include "mp_internal.cuh"
+
+#include <cudaTypedefs.h>
 
 using namespace mpg;
 
@@ -173,6 +176,10 @@ long long ceildiv(long long x, long long d) { return -floordiv(-x, d); }
 
 void plan_free(mp_plan* p) {
     if (!p) return;
+    for (int w = 0; w < MAXW; ++w) {
+        if (p->d_Ahi[w]) cudaFree(p->d_Ahi[w]);
+        if (p->d_Alo[w]) cudaFree(p->d_Alo[w]);
+    }
     for (int i = 0; i < MAXW * MAXW; ++i)
         if (p->d_kern[i]) cudaFree(p->d_kern[i]);
     for (int w = 0; w < MAXW; ++w)
@@ -185,6 +192,35 @@ void plan_free(mp_plan* p) {
 }
 
 }  // namespace
+
+bool mpg::encode_bf16_map(void* map, const void* base, unsigned long long inner,
+                          unsigned long long outer, unsigned long long row_bytes) {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !f) {
+            mpg_set_error("cuTensorMapEncodeTiled is not available");
+            return false;
+        }
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {row_bytes};
+    cuuint32_t box[2] = {64, 128};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        mpg_set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return false;
+    }
+    return true;
+}
 
 extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows,
                               const int* win_len, const int* a, const int* M, double kern_thr,
@@ -228,10 +264,19 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
             }
         }
 
+    if (flags & MP_ANALYSIS_BF16X3)
+        for (int w = 0; w < W; ++w)
+            if (a[w] % 64 || (win_len[w] / 2) % a[w]) {
+                mpg_set_error("mp_plan_create: the split-BF16 analysis needs every a to be a "
+                              "multiple of 64 and every w/2 a multiple of a (dictionary %d)", w);
+                return MP_EINVAL;
+            }
     int rc = MP_OK;
     mp_plan* p = new mp_plan();
     memset(p->d_kern, 0, sizeof(p->d_kern));
     memset(p->d_A, 0, sizeof(p->d_A));
+    memset(p->d_Ahi, 0, sizeof(p->d_Ahi));
+    memset(p->d_Alo, 0, sizeof(p->d_Alo));
     p->d_cls = nullptr;
     p->d_tiles = nullptr;
     p->d_gam = nullptr;
@@ -452,6 +497,22 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
                                                                        D.Mr, rows, p->d_A[w]);
             CK(cudaGetLastError());
         }
+        // split-BF16 operands and their tensor maps
+        if (flags & MP_ANALYSIS_BF16X3)
+            for (int w = 0; w < W; ++w) {
+                const int kp = ((p->dp.d[w].wlen + 63) / 64) * 64;
+                p->Kp64[w] = kp;
+                const size_t bytes = (size_t)p->Arows[w] * kp * 2;
+                CK(cudaMalloc(&p->d_Ahi[w], bytes));
+                CK(cudaMalloc(&p->d_Alo[w], bytes));
+                CK(launch_split_rows(p->d_A[w], p->Arows[w], p->dp.d[w].wlen, p->Akp[w], kp,
+                                     p->d_Ahi[w], p->d_Alo[w], st));
+                if (!encode_bf16_map(p->tmA[w][0], p->d_Ahi[w], kp, p->Arows[w], (size_t)kp * 2) ||
+                    !encode_bf16_map(p->tmA[w][1], p->d_Alo[w], kp, p->Arows[w], (size_t)kp * 2)) {
+                    rc = MP_ECUDA;
+                    goto fail;
+                }
+            }
         CK(cudaStreamSynchronize(st));
         p->dp.cls = p->d_cls;
         p->dp.ncls = (int)p->cls.size();

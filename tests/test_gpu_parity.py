@@ -308,3 +308,77 @@ def test_many_signals_narrow_ctas():
     for i, (x, (atoms, errs, E0, stop)) in enumerate(zip(xs, out)):
         ref = cmp.mp_coef(dicts, x.astype(np.float64), 1e-4, K, 200.0)
         compare(atoms, errs, E0, ref, min_checked=10)
+
+
+# --------------------------------------------- precision form (BF16 x 3) ---
+
+def _bf16_dicts():
+    return 16384, [(inputs.blackman(w), w // 4, w) for w in (256, 512, 1024)]
+
+
+def test_analysis_bf16x3_error_vs_oracle():
+    """Split-BF16 three-product DFT-GEMM on tcgen05: the error against the
+    FP64 analysis is about 2^-16 per product; normwise below 2e-5, largest
+    entry error below 2e-4 of the coefficients' RMS."""
+    L, dicts = _bf16_dicts()
+    x = inputs.as_f32(inputs.mixture(L, 22, fs=16000.0))
+    plan = _plan(dicts, 1e-4, mg.MP_ANALYSIS_BF16X3)
+    st = mg.mp_analyze(plan, [torch.from_numpy(x).cuda()])
+    for w, (g, a, M) in enumerate(dicts):
+        ref = cmp.dgt(x.astype(np.float64), g, a, M)
+        got = mg.mp_state_coefficients(st, 0, w)
+        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        worst = np.max(np.abs(got - ref)) / np.sqrt(np.mean(np.abs(ref) ** 2))
+        print("dict", w, "normwise", rel, "max/rms", worst)
+        assert rel < 2e-5 and worst < 2e-4
+
+
+def test_analysis_bf16x3_batched_uneven():
+    """Tensor-core analysis over several signals of different lengths in one
+    launch per dictionary (frame tiles crossing signal boundaries)."""
+    L, dicts = _bf16_dicts()
+    lens = [4096, 16384, 8192, 12288]
+    xs = [inputs.as_f32(inputs.mixture(n, 23 + i, fs=16000.0)) for i, n in enumerate(lens)]
+    plan = _plan(dicts, 1e-4, mg.MP_ANALYSIS_BF16X3)
+    st = mg.mp_analyze(plan, [torch.from_numpy(x).cuda() for x in xs])
+    for b, x in enumerate(xs):
+        for w, (g, a, M) in enumerate(dicts):
+            ref = cmp.dgt(x.astype(np.float64), g, a, M)
+            got = mg.mp_state_coefficients(st, b, w)
+            assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 2e-5
+
+
+def test_mp_bf16x3_decomposition_vs_oracle():
+    """Decomposition with the split-BF16 analysis against the FP64 oracle.
+    The analysis error (~1e-5 of the coefficient scale) can flip near ties,
+    so what is compared is what stays unique: the sequences agree up to
+    their first divergence, the oracle's gap there is below 1e-3 (a near
+    tie at this precision), coefficients before it agree within 1e-3, and
+    the SNR curves of the two valid pursuits stay within 0.1 dB."""
+    L, dicts = _bf16_dicts()
+    x = inputs.as_f32(inputs.mixture(L, 24, fs=16000.0))
+    K = 400
+    ref = cmp.mp_coef(dicts, x.astype(np.float64), 1e-4, K, 200.0)
+    plan = _plan(dicts, 1e-4, mg.MP_ANALYSIS_BF16X3)
+    st = mg.mp_analyze(plan, [torch.from_numpy(x).cuda()])
+    n, stop, q = mg.mp_run(st, K, 200.0)
+    atoms, errs = mg.mp_get_atoms(st, 0), mg.mp_get_errors(st, 0)
+    assert atoms.size == K
+    same = (atoms["dict"] == ref.dict) & (atoms["m"] == ref.m) & (atoms["n"] == ref.n)
+    d = int(np.argmin(same)) if not same.all() else K
+    if d < K:
+        gap = (ref.s1[d] - ref.s2[d]) / ref.s1[d]
+        assert gap < 1e-3, (d, gap)
+    c = atoms["re"][:d].astype(np.float64) + 1j * atoms["im"][:d]
+    if d:
+        assert np.max(np.abs(c - ref.c[:d]) / np.abs(ref.c[:d])) < 1e-3
+    E0 = errs[-1] * 10 ** (q[0] / 10)
+    dsnr = np.max(np.abs(10 * np.log10(E0 / errs) - 10 * np.log10(ref.E0 / ref.E)))
+    print("first divergence", d, "max SNR deviation", dsnr)
+    assert dsnr < 0.1
+
+
+def test_bf16x3_rejects_incompatible_hops():
+    with pytest.raises(mg.MPError) as ei:
+        _plan([(inputs.blackman(64), 16, 64)], 1e-4, mg.MP_ANALYSIS_BF16X3)
+    assert ei.value.code == mg.MP_EINVAL
