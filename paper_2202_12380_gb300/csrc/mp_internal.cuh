@@ -40,6 +40,7 @@ struct DevDict {
     int g_off;                     // offset of the FP32 window in DevPlan::g32
     int msh;                       // flat-index row stride 2^msh >= Mr
     int Mmask;                     // M - 1 if M is a power of two, else 0
+    int cis_off;                   // offset of e^{i 2 pi q / M}, q < M, in DevPlan::cis
 };
 
 struct DevPair {
@@ -62,6 +63,7 @@ struct DevPlan {
     int W;
     int ncls;  // class descriptors
     int ngam;  // entries of the compact <d, conj d> pool
+    int ncis;  // entries of the modulation tables
     int pad;
     DevDict d[MAXW];
     DevPair p[MAXW * MAXW];
@@ -69,6 +71,7 @@ struct DevPlan {
     const float2* tiles;
     const float2* gam;
     const float* g32;
+    const float2* cis;  // e^{i 2 pi q / M_w} per dictionary (FP64-rounded to FP32)
 };
 
 struct DevSig {
@@ -167,6 +170,7 @@ struct mp_plan {
     long long tiles_len;
     float2* d_gam;
     float* d_g32;
+    float2* d_cis32;
     float* d_A[mpg::MAXW];  // FP32 DFT matrices for the analysis, [Arows][Akp]
     int Arows[mpg::MAXW], Akp[mpg::MAXW];
     // split-BF16 analysis (MP_ANALYSIS_BF16X3): A = A_hi + A_lo, [Arows][Kp64]

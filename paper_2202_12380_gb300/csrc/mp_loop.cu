@@ -9,31 +9,30 @@
 // shared memory and is scanned by the whole CTA every iteration (a few
 // shared loads per thread), so there is no further level to maintain.
 //
-// One iteration, for every warp of the CTA:
-//   1. scan the top level, warp-reduce, publish the warp's best; barrier;
-//   2. reduce the per-warp bests (every warp redundantly), apply the stop
-//      tests, adjust the selected coefficient to the real-pair coefficient
-//      (eqs. dualatprod / projenfaster), accumulate E in FP64 and describe
-//      the update of every dictionary: lane 2v + t builds term t (0: the
-//      atom, 1: its conjugate partner) of dictionary v;
-//   3. run frame jobs: for each touched frame of each dictionary, load the
-//      frame's level-0 entries together with the touched 32-bin chunks of the
-//      plane and the matching class-tile entries (one round of independent
-//      loads), subtract both terms (eq. fastkernupdate with the modulation of
-//      eq. hkj), recompute the touched chunks' level-0 entries, the frame's
-//      level-1 entry and its top-level slot; barrier.
-// Every warp computes the same selection; thread 0 alone writes the atom list
-// and keeps the FP64 energy E, whose stop tests it publishes for the next
-// iteration before the closing barrier.
+// One iteration:
+//   1. every thread scans its share of the top level; warp bests are reduced
+//      to the CTA best (shared memory + barrier);
+//   2. with a cluster, each CTA sends its best to every CTA of the cluster
+//      (st.async into distributed shared memory, completing bytes on the
+//      receiver's mbarrier) and waits, bounded, for all of them; every warp
+//      then takes the same selection, adjusts the coefficient to the
+//      real-pair coefficient (eqs. dualatprod / projenfaster) and one thread
+//      keeps E in FP64 and writes the atom list;
+//   3. warps are assigned to dictionaries (warp w serves w mod W); a warp
+//      builds its dictionary's update -- the atom's and the conjugate
+//      partner's class tile, the column hull and the touched 32-bin chunks
+//      as a bit mask -- and runs one job per owned touched frame: load the
+//      frame's level-0 entries together with the touched chunks of the plane
+//      and the matching tile entries, subtract both terms (eq.
+//      fastkernupdate with the modulation of eq. hkj, looked up in an FP64-
+//      rounded table), recompute the touched chunks' level-0 entries, the
+//      frame's level-1 entry and its top-level slot; barrier.
 //
 // Clusters.  A signal may be given a thread-block cluster of CS CTAs (on CS
 // SMs) instead of one CTA: frame n of every dictionary belongs to CTA
-// n mod CS, which holds its top-level entry and runs its frame jobs.  In step
-// 1 each warp pushes its best candidate into every CTA's shared memory
-// (distributed shared memory) and the cluster barrier replaces the CTA
-// barrier; every CTA then takes the same selection.  The time limit is
-// decided by CTA 0 and pushed the same way, so all CTAs leave the loop in the
-// same iteration.
+// n mod CS, which holds its top-level entry and runs its frame jobs.  The
+// time limit is decided by CTA 0 and sent with the candidates, so all CTAs
+// leave the loop in the same iteration.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -76,20 +75,6 @@ __device__ __forceinline__ int imod(int x, int m) {
     return r < 0 ? r + m : r;
 }
 
-__device__ __forceinline__ Term shfl_term(const Term& t, int src) {
-    Term r;
-    r.active = __shfl_sync(FULL, t.active, src);
-    r.Arow = __shfl_sync(FULL, t.Arow, src);
-    r.R = __shfl_sync(FULL, t.R, src);
-    r.Acol = __shfl_sync(FULL, t.Acol, src);
-    r.C = __shfl_sync(FULL, t.C, src);
-    r.kk = __shfl_sync(FULL, t.kk, src);
-    r.tau0 = __shfl_sync(FULL, t.tau0, src);
-    r.a0 = __shfl_sync(FULL, t.a0, src);
-    r.tile = __shfl_sync(FULL, t.tile, src);
-    return r;
-}
-
 // term t of dictionary v for the selected (u, k, j)
 __device__ __forceinline__ Term make_term(const DevDict* sd, const DevPair* sp,
                                           const DevClass* scls, int W, const DevSig& S, int u,
@@ -127,19 +112,6 @@ __device__ __forceinline__ Term make_term(const DevDict* sd, const DevPair* sp,
     return T;
 }
 
-// chunk ranges [lo, hi) of a term's stored rows: up to two
-__device__ __forceinline__ int term_chunks(const Term& t, int Mv, int Mr, int* lo, int* hi) {
-    if (!t.active) return 0;
-    int n = 0;
-    const int e1 = min(min(t.Arow + t.R, Mv), Mr);
-    if (e1 > t.Arow) { lo[n] = t.Arow / CHUNK; hi[n] = (e1 - 1) / CHUNK + 1; ++n; }
-    if (t.Arow + t.R > Mv) {
-        const int b1 = min(t.Arow + t.R - Mv, Mr);
-        if (b1 > 0) { lo[n] = 0; hi[n] = (b1 - 1) / CHUNK + 1; ++n; }
-    }
-    return n;
-}
-
 __device__ __forceinline__ bool term_hit(const Term& T, int m, int n, int Mv, int Nv, int* off) {
     if (!T.active) return false;
     int cc = n - T.Acol;
@@ -152,27 +124,158 @@ __device__ __forceinline__ bool term_hit(const Term& T, int m, int n, int Mv, in
     return true;
 }
 
-__device__ __forceinline__ float2 term_phase(const Term& T, int n, int Nv, int av, int Mu,
-                                             int Mumask) {
+// index q = (k tau) mod M_u of the column's modulation e^{i 2 pi k tau / M_u}
+__device__ __forceinline__ int term_q(const Term& T, int n, int Nv, int av, int Mu, int Mumask) {
     int cc = n - T.Acol;
     if (cc < 0) cc += Nv;
     const int tau = T.tau0 + cc * av;
-    unsigned q;
-    if (Mumask) {
-        q = ((unsigned)T.kk * ((unsigned)tau & (unsigned)Mumask)) & (unsigned)Mumask;
-    } else {
-        const unsigned tm = (unsigned)imod(tau, Mu);
-        q = ((unsigned)T.kk * tm) % (unsigned)Mu;
-    }
-    float sn, cs;
-    sincospif(2.0f * (float)q / (float)Mu, &sn, &cs);
-    return make_float2(cs, sn);
+    if (Mumask) return (int)(((unsigned)T.kk * ((unsigned)tau & (unsigned)Mumask)) & (unsigned)Mumask);
+    const unsigned tm = (unsigned)imod(tau, Mu);
+    return (int)(((unsigned long long)T.kk * tm) % (unsigned)Mu);
 }
 
 __device__ __forceinline__ float2 gamma_of(const DevDict& D, const float2* sgam, int k) {
     if (k < D.gam_lo) return sgam[D.gam_off + k];
     if (k >= D.Mr - D.gam_hi) return sgam[D.gam_off + D.gam_lo + (k - (D.Mr - D.gam_hi))];
     return make_float2(0.f, 0.f);
+}
+
+__device__ __forceinline__ unsigned mapa_u32(unsigned addr, int rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+// 16-byte store into another CTA's shared memory that also completes 16
+// bytes of transaction on that CTA's mbarrier
+__device__ __forceinline__ void st_async16(unsigned raddr, const Entry& e, unsigned rbar) {
+    const unsigned k0 = (unsigned)e.key, k1 = (unsigned)(e.key >> 32);
+    asm volatile(
+        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];"
+        :
+        : "r"(raddr), "r"(k0), "r"(k1), "r"(__float_as_uint(e.val.x)), "r"(__float_as_uint(e.val.y)),
+          "r"(rbar)
+        : "memory");
+}
+
+__device__ __forceinline__ bool xbar_try(unsigned addr, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// one dictionary's part of the update, shared by the warps that serve it;
+// all fields are scalars so the struct lives in registers
+struct DictJob {
+    Term t0, t1;
+    int nstart;  // first frame of the hull owned by this CTA
+    int cnt;     // owned frames of the hull
+    // chunk ranges [l, h): a0, a1 of the atom (na of them), b0, b1 of the
+    // partner (nb of them)
+    int a0l, a0h, a1l, a1h, b0l, b0h, b1l, b1h;
+    int na, nb;
+    // the same set as a bit mask over chunks cbase .. cbase + 63 (cwide: the
+    // set spans more than 64 chunks and is walked range by range instead)
+    int cbase, cend;
+    unsigned long long cmask;
+    bool cwide;
+};
+
+// chunk ranges of a term's stored rows: up to two, as scalars
+__device__ __forceinline__ int term_chunks2(const Term& t, int Mv, int Mr, int& l0, int& h0, int& l1,
+                                            int& h1) {
+    l0 = h0 = l1 = h1 = 0;
+    if (!t.active) return 0;
+    int n = 0;
+    const int e1 = min(min(t.Arow + t.R, Mv), Mr);
+    if (e1 > t.Arow) {
+        l0 = t.Arow / CHUNK;
+        h0 = (e1 - 1) / CHUNK + 1;
+        n = 1;
+    }
+    if (t.Arow + t.R > Mv) {
+        const int b1 = min(t.Arow + t.R - Mv, Mr);
+        if (b1 > 0) {
+            const int l = 0, h = (b1 - 1) / CHUNK + 1;
+            if (n == 0) { l0 = l; h0 = h; } else { l1 = l; h1 = h; }
+            ++n;
+        }
+    }
+    return n;
+}
+
+__device__ __forceinline__ bool in_ranges(const DictJob& J, int c) {
+    bool t = false;
+    t |= (J.na > 0) & (c >= J.a0l) & (c < J.a0h);
+    t |= (J.na > 1) & (c >= J.a1l) & (c < J.a1h);
+    t |= (J.nb > 0) & (c >= J.b0l) & (c < J.b0h);
+    t |= (J.nb > 1) & (c >= J.b1l) & (c < J.b1h);
+    return t;
+}
+
+
+__device__ __forceinline__ void dict_job(const DevDict* sd, const DevPair* sp, const DevClass* scls,
+                                         int W, const DevSig& S, int u, int kk, int j, bool edge,
+                                         int v, int rank, int CS, DictJob& J) {
+    J.t0 = make_term(sd, sp, scls, W, S, u, kk, j, edge, v, 0);
+    J.t1 = make_term(sd, sp, scls, W, S, u, kk, j, edge, v, 1);
+    const DevDict& Dv = sd[v];
+    const int Nv = (int)S.N[v];
+    J.cnt = 0;
+    J.nstart = 0;
+    int lo = 0, hi = 0;
+    bool any = false;
+    if (J.t0.active) { lo = J.t0.a0; hi = J.t0.a0 + J.t0.C; any = true; }
+    if (J.t1.active) {
+        if (any) { lo = min(lo, J.t1.a0); hi = max(hi, J.t1.a0 + J.t1.C); }
+        else { lo = J.t1.a0; hi = J.t1.a0 + J.t1.C; any = true; }
+    }
+    if (any) {
+        int ns, nf;
+        const int nc = hi - lo;
+        if (nc >= Nv) { ns = 0; nf = Nv; }
+        else { ns = S.Nmask[v] ? (lo & S.Nmask[v]) : imod(lo, Nv); nf = nc; }
+        const int i0 = imod(rank - ns, CS);
+        J.nstart = ns + i0;
+        J.cnt = nf > i0 ? (nf - i0 + CS - 1) / CS : 0;
+    }
+    J.na = term_chunks2(J.t0, Dv.M, Dv.Mr, J.a0l, J.a0h, J.a1l, J.a1h);
+    J.nb = term_chunks2(J.t1, Dv.M, Dv.Mr, J.b0l, J.b0h, J.b1l, J.b1h);
+    int clo = 1 << 30, chi = 0;
+    if (J.na > 0) { clo = min(clo, J.a0l); chi = max(chi, J.a0h); }
+    if (J.na > 1) { clo = min(clo, J.a1l); chi = max(chi, J.a1h); }
+    if (J.nb > 0) { clo = min(clo, J.b0l); chi = max(chi, J.b0h); }
+    if (J.nb > 1) { clo = min(clo, J.b1l); chi = max(chi, J.b1h); }
+    if (chi <= clo) { clo = 0; chi = 0; }
+    J.cbase = clo;
+    J.cend = chi;
+    J.cwide = chi - clo > 64;
+    unsigned long long m = 0;
+    if (!J.cwide) {
+        auto add = [&](int l, int h) {
+            const int n = h - l;
+            const unsigned long long bits = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
+            m |= bits << (l - clo);
+        };
+        if (J.na > 0) add(J.a0l, J.a0h);
+        if (J.na > 1) add(J.a1l, J.a1h);
+        if (J.nb > 0) add(J.b0l, J.b0h);
+        if (J.nb > 1) add(J.b1l, J.b1h);
+    }
+    J.cmask = m;
+}
+
+__device__ __forceinline__ bool chunk_touched(const DictJob& J, int c) {
+    if (!J.cwide) {
+        const int d = c - J.cbase;
+        return d >= 0 && d < 64 && ((J.cmask >> d) & 1ull);
+    }
+    return in_ranges(J, c);
 }
 
 template <int NT>
@@ -185,9 +288,12 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     __shared__ DevSig S;
     __shared__ DevDict sd[MAXW];
     __shared__ DevPair sp[MAXW * MAXW];
-    __shared__ int sstop[2];  // stop decision per iteration parity
-    __shared__ int cflag[2];  // time-limit decision of CTA 0, per parity
-    __shared__ int ltb[MAXW + 1];  // local top-level base per dictionary
+    __shared__ int sstop[2];        // stop decision per iteration parity
+    __shared__ int ltb[MAXW + 1];   // local top-level base per dictionary
+    __shared__ Entry wsel[NWARPS];  // per-warp bests of the scan
+    __shared__ __align__(16) Entry cand[2][16];      // CTA bests of the cluster, per parity
+    __shared__ __align__(16) int tmsg[2][4];         // time-limit message of CTA 0, per parity
+    __shared__ __align__(8) unsigned long long xbar[2];  // exchange barriers, per parity
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = CS > 1 ? (int)cluster.block_rank() : 0;
     DevSig& Sg = sigs[order[blockIdx.x / CS]];
@@ -200,9 +306,15 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     const int W = P.W;
     for (int i = tid; i < W; i += NT) sd[i] = P.d[i];
     for (int i = tid; i < W * W; i += NT) sp[i] = P.p[i];
+    const unsigned xb0 = (unsigned)__cvta_generic_to_shared(&xbar[0]);
+    const unsigned xb1 = (unsigned)__cvta_generic_to_shared(&xbar[1]);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(xb0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(xb1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tmsg[0][0] = tmsg[1][0] = 0;
+    }
     __syncthreads();
-    // top level of this CTA: all frames (CS == 1, with frame groups when
-    // 2^gshift > 1) or the frames n = rank (mod CS) (CS > 1, gshift == 0)
     if (tid == 0) {
         int b = 0;
         for (int w = 0; w < W; ++w) {
@@ -210,19 +322,18 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
             b += CS > 1 ? (int)(S.N[w] / CS) : S.tbase[w + 1] - S.tbase[w];
         }
         ltb[W] = b;
-        cflag[0] = cflag[1] = 0;
     }
     __syncthreads();
     const int T = ltb[W];
-    const int NC = CS * NWARPS;  // candidates exchanged per iteration
-    Entry* cand = reinterpret_cast<Entry*>(smem_raw);           // [2][NC]
-    Entry* top = cand + 2 * NC;
+    Entry* top = reinterpret_cast<Entry*>(smem_raw);
     DevClass* scls = reinterpret_cast<DevClass*>(top + T);
     float2* sgam = reinterpret_cast<float2*>(scls + P.ncls);
-    unsigned char* tdirty = reinterpret_cast<unsigned char*>(sgam + P.ngam);
+    float2* scis = sgam + P.ngam;
+    unsigned char* tdirty = reinterpret_cast<unsigned char*>(scis + P.ncis);
 
     for (int i = tid; i < P.ncls; i += NT) scls[i] = P.cls[i];
     for (int i = tid; i < P.ngam; i += NT) sgam[i] = P.gam[i];
+    for (int i = tid; i < P.ncis; i += NT) scis[i] = P.cis[i];
     for (int w = 0; w < W; ++w) {
         const int tb = ltb[w], te = ltb[w + 1];
         if (CS > 1) {
@@ -233,19 +344,20 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         }
     }
     for (int i = tid; i < T; i += NT) tdirty[i] = 0;
-    if (CS > 1) cluster.sync(); else __syncthreads();
 
     long long k = S.k;
-    // FP64 work stays in thread 0 (the FP64 pipe is narrow on this part):
+    // FP64 work stays in one thread (the FP64 pipe is narrow on this part):
     // E, and the stop tests that read it, are evaluated there one iteration
     // ahead and published in sstop
+    const int KEEPER = NT - 32;
     double E = S.E;
     const double E0 = S.E0;
     const double thr = E0 * thr_scale;
     const unsigned long long t_start = gtimer();
     const float2* __restrict__ tiles = P.tiles;
+    const unsigned xbytes = (unsigned)(CS * sizeof(Entry)) + (budget_ns > 0 ? 16u : 0u);
     int stop = 0;
-    if (tid == NT - 32) {
+    if (tid == KEEPER) {
         int s0 = 0;
         if (!isfinite(E0)) s0 = MP_STOP_INVALID;
         else if (E <= 0.0) s0 = MP_STOP_NEGENERGY;
@@ -253,10 +365,17 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         else if (k >= kmax) s0 = MP_STOP_KMAX;
         sstop[k & 1] = s0;
     }
-    __syncthreads();
+    // every CTA's barriers are initialised before anyone sends
+    if (CS > 1) cluster.sync(); else __syncthreads();
 
+    // warp -> dictionary service: warp w serves v = w mod W as its slot w / W
+    // of nserve(v) warps (or, with fewer warps than dictionaries, v = w,
+    // w + NWARPS, ...)
+    unsigned long long it = 0;  // iteration counter (exchange parities)
     for (;;) {
-        // ---- 1. scan of the top level ------------------------------------
+        const int par = (int)(it & 1);
+        const unsigned xb = par ? xb1 : xb0;
+        // ---- 1. scan of the top level, CTA best, cluster exchange ----------
         {
             Entry b;
             b.key = 0;
@@ -266,45 +385,66 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                 if (e.key > b.key) b = e;
             }
             const Entry r = warp_max_entry(b);
-            Entry* slot = cand + (k & 1) * NC + rank * NWARPS + warp;
-            // the time limit is read once per iteration by one thread (of CTA
-            // 0) so that every warp of every CTA takes the same decision
-            if (CS > 1) {
-                if (lane < CS) {
-                    Entry* rs = static_cast<Entry*>(__cluster_map_shared_rank(slot, lane));
-                    *rs = r;
-                }
-            } else if (lane == 0) {
-                *slot = r;
-            }
-            if (budget_ns > 0 && rank == 0 && warp == 0) {
-                int tflag = 0;
-                if (lane == 0) tflag = (long long)(gtimer() - t_start) > budget_ns ? 1 : 0;
-                tflag = __shfl_sync(FULL, tflag, 0);
-                if (lane < CS) {
-                    int* rf = CS > 1 ? static_cast<int*>(__cluster_map_shared_rank(&cflag[k & 1], lane))
-                                     : &cflag[k & 1];
-                    *rf = tflag;
-                }
-            }
+            if (lane == 0) wsel[warp] = r;
+            if (CS > 1 && tid == 0)
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(xb),
+                             "r"(xbytes)
+                             : "memory");
         }
-        if (CS > 1) cluster.sync(); else __syncthreads();
-
-        // ---- 2. selection, adjustment, update description (every warp) --
+        __syncthreads();
         Entry best;
         {
             Entry b;
             b.key = 0;
             b.val = make_float2(0.f, 0.f);
-            const Entry* cb = cand + (k & 1) * NC;
-            for (int i = lane; i < NC; i += 32) {
-                const Entry e = cb[i];
-                if (e.key > b.key) b = e;
-            }
+            if (lane < NWARPS) b = wsel[lane];
             best = warp_max_entry(b);
         }
-        stop = sstop[k & 1];
-        if (stop == 0 && cflag[k & 1]) stop = -1;
+        if (CS > 1) {
+            if (warp == 0) {
+                if (lane < CS) {
+                    const unsigned laddr = (unsigned)__cvta_generic_to_shared(&cand[par][rank]);
+                    st_async16(mapa_u32(laddr, lane), best, mapa_u32(xb, lane));
+                }
+                if (budget_ns > 0 && rank == 0) {
+                    int tf = 0;
+                    if (lane == 0) tf = (long long)(gtimer() - t_start) > budget_ns ? 1 : 0;
+                    tf = __shfl_sync(FULL, tf, 0);
+                    if (lane < CS) {
+                        Entry m;
+                        m.key = (unsigned long long)(unsigned)tf;
+                        m.val = make_float2(0.f, 0.f);
+                        const unsigned laddr = (unsigned)__cvta_generic_to_shared(&tmsg[par][0]);
+                        st_async16(mapa_u32(laddr, lane), m, mapa_u32(xb, lane));
+                    }
+                }
+            }
+            // bounded wait for the CS candidates (and the time-limit message)
+            const unsigned long long w0 = gtimer();
+            const unsigned xpar = (unsigned)((it >> 1) & 1);
+            bool ok = true;
+            while (!xbar_try(xb, xpar)) {
+                if (gtimer() - w0 > 2000000000ull) {
+                    ok = false;
+                    break;
+                }
+            }
+            Entry b;
+            b.key = 0;
+            b.val = make_float2(0.f, 0.f);
+            if (lane < CS) b = cand[par][lane];
+            best = warp_max_entry(b);
+            if (!ok) stop = -2;
+        } else if (budget_ns > 0) {
+            // single CTA: the time limit is read by one thread before the scan
+            // barrier of the next iteration; here it is read after this one
+            if (tid == 0) tmsg[par][0] = (long long)(gtimer() - t_start) > budget_ns ? 1 : 0;
+            __syncthreads();
+        }
+
+        // ---- 2. selection, adjustment, bookkeeping -------------------------
+        if (stop == 0) stop = sstop[k & 1];
+        if (stop == 0 && budget_ns > 0 && tmsg[par][0]) stop = -1;
         if (stop == 0 && (unsigned)(best.key >> 32) == 0u) stop = MP_STOP_ZEROMAX;
         if (stop) break;
 
@@ -316,6 +456,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         const int kk = (int)(rel & ((1u << sd[u].msh) - 1u));
         const int Mu = sd[u].M;
         const int Mumask = sd[u].Mmask;
+        const float2* cis_u = scis + sd[u].cis_off;
         const bool edge = (kk == 0) || (2 * kk == Mu);
         // eqs. dualatprod / projenfaster: coefficient and energy drop in FP32
         // (gamma is zero away from m = 0 and m = M/2), E accumulated in FP64
@@ -339,23 +480,18 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                 Edf = 2.f * (c2 + fmaf(g.x, d2, -2.f * g.y * cx * cy));
             }
         }
-        // bookkeeping (FP64 energy, atom list, next stop decision) in lane 0 of
-        // the last warp, which the frame jobs reach last
-        const bool keeper = (tid == NT - 32);
-        if (keeper) {
+        if (tid == KEEPER) {
             E -= (double)Edf;
-        }
-        if (keeper && rank == 0) {
-            mp_atom at;
-            at.dict = u;
-            at.m = kk;
-            at.n = j;
-            at.re = cx;
-            at.im = cy;
-            S.atoms[k] = at;
-            S.errs[k] = E;
-        }
-        if (keeper) {
+            if (rank == 0) {
+                mp_atom at;
+                at.dict = u;
+                at.m = kk;
+                at.n = j;
+                at.re = cx;
+                at.im = cy;
+                S.atoms[k] = at;
+                S.errs[k] = E;
+            }
             int s1 = 0;  // stop tests before the next selection
             if (E <= 0.0) s1 = MP_STOP_NEGENERGY;
             else if (E <= thr) s1 = MP_STOP_SNR;
@@ -364,179 +500,134 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         }
         ++k;
         const float2 c_main = make_float2(cx, cy), c_conj = make_float2(cx, -cy);
-        // lane 2v + t describes term t of dictionary v
-        Term mine;
-        {
-            const int v = lane >> 1, t = lane & 1;
-            if (v < W) {
-                mine = make_term(sd, sp, scls, W, S, u, kk, j, edge, v, t);
-            } else {
-                mine.active = 0;
-                mine.Arow = mine.R = mine.Acol = mine.C = mine.kk = mine.tau0 = mine.a0 = 0;
-                mine.tile = 0;
-            }
-        }
-        // frame counts per dictionary: column hull of its active terms
-        int nframes = 0, nstart = 0;  // meaningful in lanes 2v
-        {
-            const int oa = __shfl_xor_sync(FULL, mine.active, 1);
-            const int oa0 = __shfl_xor_sync(FULL, mine.a0, 1);
-            const int oc = __shfl_xor_sync(FULL, mine.C, 1);
-            if ((lane & 1) == 0 && (lane >> 1) < W) {
-                int lo = 0, hi = 0;
-                bool any = false;
-                if (mine.active) { lo = mine.a0; hi = mine.a0 + mine.C; any = true; }
-                if (oa) {
-                    if (any) { lo = min(lo, oa0); hi = max(hi, oa0 + oc); }
-                    else { lo = oa0; hi = oa0 + oc; any = true; }
-                }
-                if (any) {
-                    const int Nv = (int)S.N[lane >> 1];
-                    const int nc = hi - lo;
-                    if (nc >= Nv) { nstart = 0; nframes = Nv; }
-                    else { nstart = imod(lo, Nv); nframes = nc; }
-                    // frames of the hull owned by this CTA: i = i0, i0 + CS, ...
-                    const int i0 = imod(rank - nstart, CS);
-                    nstart += i0;  // first owned frame (may reach N_v: wrapped below)
-                    nframes = nframes > i0 ? (nframes - i0 + CS - 1) / CS : 0;
-                }
-            }
-        }
-        // inclusive prefix of frame counts over v (held in lanes 0, 2, 4, ...)
-        int pre = nframes;
-#pragma unroll
-        for (int o = 2; o < 2 * MAXW; o <<= 1) {
-            const int x = __shfl_up_sync(FULL, pre, o);
-            if (lane >= o) pre += x;
-        }
-        const int total = __shfl_sync(FULL, pre, 2 * W - 2);
 
-        // ---- 3. frame jobs -------------------------------------------------
-        for (int g = warp; g < total; g += NWARPS) {
-            // dictionary: number of inclusive prefixes <= g
-            int v = 0;
-            for (int q = 0; q < W; ++q) {
-                const int pq = __shfl_sync(FULL, pre, 2 * q);
-                v += (pq <= g) ? 1 : 0;
-            }
-            const int pv = __shfl_sync(FULL, pre, 2 * v);
-            const int fv = __shfl_sync(FULL, nframes, 2 * v);
-            const int sv = __shfl_sync(FULL, nstart, 2 * v);
-            const Term t0 = shfl_term(mine, 2 * v);
-            const Term t1 = shfl_term(mine, 2 * v + 1);
+        // ---- 3. frame jobs: each warp serves its dictionaries ---------------
+        // warp w serves dictionary w mod W as slot w / W of the warps that
+        // serve it; with fewer warps than dictionaries it serves w, w +
+        // NWARPS, ... alone
+        const int v_first = NWARPS >= W ? warp % W : warp;
+        const int v_step = NWARPS >= W ? W : NWARPS;
+        const int slot = NWARPS >= W ? warp / W : 0;
+        for (int v = v_first; v < W; v += v_step) {
+            const int nserve = NWARPS >= W ? (NWARPS / W + (v < NWARPS % W ? 1 : 0)) : 1;
+            DictJob J;
+            dict_job(sd, sp, scls, W, S, u, kk, j, edge, v, rank, CS, J);
             const DevDict& Dv = sd[v];
             const int Nv = (int)S.N[v];
-            int n = sv + (g - (pv - fv)) * CS;
-            if (n >= Nv) n -= Nv;
-            // level-0 entries of the whole frame (untouched chunks keep theirs)
-            const Entry* l0row = S.l0[v] + (long long)n * Dv.nch;
-            Entry l0v[MAXL0];
+            for (int f = slot; f < J.cnt; f += nserve) {
+                int n = J.nstart + f * CS;
+                n -= (n >= Nv) ? Nv : 0;
+                n -= (n >= Nv) ? Nv : 0;
+                // level-0 entries of the whole frame (untouched chunks keep theirs)
+                const Entry* l0row = S.l0[v] + (long long)n * Dv.nch;
+                Entry l0v[MAXL0];
 #pragma unroll
-            for (int q = 0; q < MAXL0; ++q) {
-                const int c = lane + 32 * q;
-                if (c < Dv.nch) l0v[q] = l0row[c];
-            }
-            // chunk list: the atom's ranges, then the partner's outside them
-            int lo[4], hi[4];
-            const int nr0 = term_chunks(t0, Dv.M, Dv.Mr, lo, hi);
-            const int nr1 = term_chunks(t1, Dv.M, Dv.Mr, lo + nr0, hi + nr0);
-            const int nr = nr0 + nr1;
-            float2* prow = S.plane[v] + (long long)n * Dv.Mrp;
-            const float2 w0 =
-                t0.active ? cmul(c_main, term_phase(t0, n, Nv, Dv.a, Mu, Mumask)) : make_float2(0.f, 0.f);
-            const float2 w1 =
-                t1.active ? cmul(c_conj, term_phase(t1, n, Nv, Dv.a, Mu, Mumask)) : make_float2(0.f, 0.f);
-            Entry fmax;
-            fmax.key = 0;
-            fmax.val = make_float2(0.f, 0.f);
-            // walk the chunks of ranges 0..nr-1, skipping partner chunks that
-            // the atom's ranges already cover
-            int r = 0, c = nr > 0 ? lo[0] : 0;
-            while (r < nr) {
-                int chunk[CB];
-                int cnt = 0;
-                while (cnt < CB && r < nr) {
-                    bool dup = false;
-                    if (r >= nr0)
-                        for (int q = 0; q < nr0; ++q) dup |= (c >= lo[q] && c < hi[q]);
-                    if (!dup) chunk[cnt++] = c;
-                    if (++c >= hi[r]) {
-                        ++r;
-                        if (r < nr) c = lo[r];
-                    }
+                for (int q = 0; q < MAXL0; ++q) {
+                    const int c = lane + 32 * q;
+                    if (c < Dv.nch) l0v[q] = l0row[c];
                 }
-                float2 val[CB], h0[CB], h1[CB];
-                bool hit0[CB], hit1[CB];
+                float2* prow = S.plane[v] + (long long)n * Dv.Mrp;
+                const float2 w0 = J.t0.active ? cmul(c_main, cis_u[term_q(J.t0, n, Nv, Dv.a, Mu, Mumask)])
+                                              : make_float2(0.f, 0.f);
+                const float2 w1 = J.t1.active ? cmul(c_conj, cis_u[term_q(J.t1, n, Nv, Dv.a, Mu, Mumask)])
+                                              : make_float2(0.f, 0.f);
+                Entry fmax;
+                fmax.key = 0;
+                fmax.val = make_float2(0.f, 0.f);
+                // touched chunks, CB at a time, lowest first (bit mask; a set
+                // wider than 64 chunks is walked chunk by chunk)
+                unsigned long long mrest = J.cmask;
+                int wc = J.cbase;
+                for (;;) {
+                    int chunk[CB];
+                    int cnt = 0;
 #pragma unroll
-                for (int q = 0; q < CB; ++q) {
-                    hit0[q] = hit1[q] = false;
-                    if (q < cnt) {
-                        const int m = chunk[q] * CHUNK + lane;
-                        val[q] = prow[m];
-                        int off;
-                        if (m < Dv.Mr) {
-                            if (term_hit(t0, m, n, Dv.M, Nv, &off)) {
-                                hit0[q] = true;
-                                h0[q] = __ldg(tiles + t0.tile + off);
+                    for (int q = 0; q < CB; ++q) {
+                        chunk[q] = -1;
+                        if (!J.cwide) {
+                            if (mrest) {
+                                const int b = __ffsll((long long)mrest) - 1;
+                                mrest &= mrest - 1ull;
+                                chunk[q] = J.cbase + b;
                             }
-                            if (term_hit(t1, m, n, Dv.M, Nv, &off)) {
-                                hit1[q] = true;
-                                h1[q] = __ldg(tiles + t1.tile + off);
+                        } else {
+                            while (wc < J.cend && !in_ranges(J, wc)) ++wc;
+                            if (wc < J.cend) chunk[q] = wc++;
+                        }
+                        cnt += chunk[q] >= 0 ? 1 : 0;
+                    }
+                    if (cnt == 0) break;
+                    float2 val[CB], h0[CB], h1[CB];
+                    bool hit0[CB], hit1[CB];
+#pragma unroll
+                    for (int q = 0; q < CB; ++q) {
+                        hit0[q] = hit1[q] = false;
+                        if (chunk[q] >= 0) {
+                            const int m = chunk[q] * CHUNK + lane;
+                            val[q] = prow[m];
+                            int off;
+                            if (m < Dv.Mr) {
+                                if (term_hit(J.t0, m, n, Dv.M, Nv, &off)) {
+                                    hit0[q] = true;
+                                    h0[q] = __ldg(tiles + J.t0.tile + off);
+                                }
+                                if (term_hit(J.t1, m, n, Dv.M, Nv, &off)) {
+                                    hit1[q] = true;
+                                    h1[q] = __ldg(tiles + J.t1.tile + off);
+                                }
                             }
                         }
                     }
-                }
 #pragma unroll
-                for (int q = 0; q < CB; ++q) {
-                    if (q >= cnt) continue;
-                    const int m = chunk[q] * CHUNK + lane;
-                    float2 x2 = val[q];
-                    if (hit0[q]) {
-                        const float2 d = cmul(w0, h0[q]);
-                        x2.x -= d.x;
-                        x2.y -= d.y;
+                    for (int q = 0; q < CB; ++q) {
+                        if (chunk[q] < 0) continue;
+                        const int m = chunk[q] * CHUNK + lane;
+                        float2 x2 = val[q];
+                        if (hit0[q]) {
+                            const float2 d = cmul(w0, h0[q]);
+                            x2.x -= d.x;
+                            x2.y -= d.y;
+                        }
+                        if (hit1[q]) {
+                            const float2 d = cmul(w1, h1[q]);
+                            x2.x -= d.x;
+                            x2.y -= d.y;
+                        }
+                        if (hit0[q] || hit1[q]) prow[m] = x2;
+                        Entry e;
+                        e.val = x2;
+                        e.key = (m < Dv.Mr) ? make_key(x2, S.fbase[v] + ((unsigned)n << Dv.msh) + m)
+                                            : 0ull;
+                        const Entry rr = warp_max_entry(e);
+                        if (lane == 0) S.l0[v][(long long)n * Dv.nch + chunk[q]] = rr;
+                        if (rr.key > fmax.key) fmax = rr;
                     }
-                    if (hit1[q]) {
-                        const float2 d = cmul(w1, h1[q]);
-                        x2.x -= d.x;
-                        x2.y -= d.y;
-                    }
-                    if (hit0[q] || hit1[q]) prow[m] = x2;
-                    Entry e;
-                    e.val = x2;
-                    e.key = (m < Dv.Mr) ? make_key(x2, S.fbase[v] + ((unsigned)n << Dv.msh) + m) : 0ull;
-                    const Entry rr = warp_max_entry(e);
-                    if (lane == 0) S.l0[v][(long long)n * Dv.nch + chunk[q]] = rr;
-                    if (rr.key > fmax.key) fmax = rr;
+                }
+                // frame maximum: untouched chunks from level 0, touched ones recomputed
+                Entry b = fmax;
+#pragma unroll
+                for (int q = 0; q < MAXL0; ++q) {
+                    const int cq = lane + 32 * q;
+                    if (cq < Dv.nch && !chunk_touched(J, cq) && l0v[q].key > b.key) b = l0v[q];
+                }
+                for (int cq = lane + 32 * MAXL0; cq < Dv.nch; cq += 32) {
+                    if (chunk_touched(J, cq)) continue;
+                    const Entry e = l0row[cq];
+                    if (e.key > b.key) b = e;
+                }
+                const Entry fr = warp_max_entry(b);
+                if (lane == 0) {
+                    S.l1[v][n] = fr;
+                    if (CS > 1) top[ltb[v] + n / CS] = fr;
+                    else if (S.gshift == 0) top[ltb[v] + n] = fr;
+                    else tdirty[ltb[v] + (n >> S.gshift)] = 1;
                 }
             }
-            // frame maximum: untouched chunks from level 0, touched ones recomputed
-            Entry b = fmax;
-#pragma unroll
-            for (int q = 0; q < MAXL0; ++q) {
-                const int cq = lane + 32 * q;
-                bool touched = false;
-                for (int z = 0; z < nr; ++z) touched |= (cq >= lo[z] && cq < hi[z]);
-                if (cq < Dv.nch && !touched && l0v[q].key > b.key) b = l0v[q];
-            }
-            for (int cq = lane + 32 * MAXL0; cq < Dv.nch; cq += 32) {
-                bool touched = false;
-                for (int z = 0; z < nr; ++z) touched |= (cq >= lo[z] && cq < hi[z]);
-                if (touched) continue;
-                const Entry e = l0row[cq];
-                if (e.key > b.key) b = e;
-            }
-            const Entry fr = warp_max_entry(b);
-            if (lane == 0) {
-                S.l1[v][n] = fr;
-                if (CS > 1) top[ltb[v] + n / CS] = fr;
-                else if (S.gshift == 0) top[ltb[v] + n] = fr;
-                else tdirty[ltb[v] + (n >> S.gshift)] = 1;
-            }
+            if (NWARPS >= W) break;  // one dictionary per warp
         }
         __syncthreads();
 
-        // ---- level 2 (groups) of touched frames --------------------------
+        // ---- level 2 (groups) of touched frames (single-CTA launches) -------
         if (CS == 1 && S.gshift > 0) {
             for (int base = warp * 32; base < T; base += NWARPS * 32) {
                 const int i = base + lane;
@@ -566,9 +657,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
             }
             __syncthreads();
         }
+        ++it;
     }
     if (CS > 1) cluster.sync();  // no CTA leaves while others may address it
-    if (tid == NT - 32 && rank == 0) {
+    if (tid == KEEPER && rank == 0) {
         Sg.k = k;
         Sg.E = E;
         if (stop > 0) {
@@ -638,9 +730,9 @@ int max_clusters(int cs, size_t smem) {
 
 }  // namespace
 
-size_t mp_loop_smem_bytes(const DevPlan& P, int T, int threads, int cs) {
-    size_t b = (size_t)2 * cs * (threads / 32) * sizeof(Entry) + (size_t)T * sizeof(Entry) +
-               (size_t)P.ncls * sizeof(DevClass) + (size_t)P.ngam * sizeof(float2) + (size_t)T;
+size_t mp_loop_smem_bytes(const DevPlan& P, int T, int, int) {
+    size_t b = (size_t)T * sizeof(Entry) + (size_t)P.ncls * sizeof(DevClass) +
+               (size_t)(P.ngam + P.ncis) * sizeof(float2) + (size_t)T;
     return (b + 15) & ~(size_t)15;
 }
 

@@ -46,6 +46,16 @@ __global__ void k_cis_table(double2* cs, int M) {
     cs[q] = make_double2(c, -s);
 }
 
+// e^{+i 2 pi q / M} rounded to FP32 (modulation of eq. hkj, looked up at
+// update time)
+__global__ void k_cis32(float2* cs, int M) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= M) return;
+    double s, c;
+    sincospi(2.0 * (double)q / (double)M, &s, &c);
+    cs[q] = make_float2((float)c, (float)s);
+}
+
 // h[it][delta] by direct sum over the window overlap (FP64)
 __global__ void k_kernel_fp64(const double* __restrict__ gu, int wu, const double* __restrict__ gv,
                               int wv, int Mx, int an, int tmin, int ntau,
@@ -155,8 +165,6 @@ __global__ void k_dft_matrix(const double* __restrict__ g, int w, int Kp, int M,
     A[idx] = o;
 }
 
-int ceil_div_ll(long long x, long long d) { return (int)((x + d - 1) / d); }
-
 long long floordiv(long long x, long long d) {
     long long q = x / d;
     if ((x % d != 0) && ((x < 0) != (d < 0))) q -= 1;
@@ -188,6 +196,7 @@ void plan_free(mp_plan* p) {
     if (p->d_tiles) cudaFree(p->d_tiles);
     if (p->d_gam) cudaFree(p->d_gam);
     if (p->d_g32) cudaFree(p->d_g32);
+    if (p->d_cis32) cudaFree(p->d_cis32);
     delete p;
 }
 
@@ -281,6 +290,7 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
     p->d_tiles = nullptr;
     p->d_gam = nullptr;
     p->d_g32 = nullptr;
+    p->d_cis32 = nullptr;
     p->W = W;
     p->eps = kern_thr;
     p->flags = flags;
@@ -326,11 +336,23 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
                                cudaMemcpyHostToDevice, st));
             CK(cudaStreamSynchronize(st));
         }
+        // FP32 modulation tables, one per dictionary
+        {
+            int tot = 0;
+            for (int w = 0; w < W; ++w) {
+                p->dp.d[w].cis_off = tot;
+                tot += M[w];
+            }
+            p->dp.ncis = tot;
+            CK(cudaMalloc(&p->d_cis32, sizeof(float2) * tot));
+            for (int w = 0; w < W; ++w) {
+                k_cis32<<<(M[w] + 255) / 256, 256, 0, st>>>(p->d_cis32 + p->dp.d[w].cis_off, M[w]);
+                CK(cudaGetLastError());
+            }
+        }
         // cis tables per distinct M_max
         int Mmax_all = 0;
         for (int w = 0; w < W; ++w) Mmax_all = std::max(Mmax_all, M[w]);
-        double2* d_cs_all = nullptr;  // one table per dictionary M (M_max of a pair is some M_w)
-        (void)d_cs_all;
         for (int w = 0; w < W; ++w) {
             CK(cudaMalloc(&d_cis[w], sizeof(double2) * M[w]));
             k_cis_table<<<(M[w] + 255) / 256, 256, 0, st>>>(d_cis[w], M[w]);
@@ -520,6 +542,7 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
         p->dp.tiles = p->d_tiles;
         p->dp.gam = p->d_gam;
         p->dp.g32 = p->d_g32;
+        p->dp.cis = p->d_cis32;
     }
     for (int w = 0; w < W; ++w) {
         cudaFree(d_win[w]);
