@@ -162,6 +162,20 @@ int mp_get_status(mp_state* state, int64_t* n_atoms, int* stop_reason, double* f
 /* seconds of device time after which a launch returns MP_ETIMEOUT (<= 0: none) */
 int mp_state_set_time_limit(mp_state* state, double seconds);
 
+/*
+ * Resets, Alg. 2 (the paper's reset options, Sec. 7): mp_run interrupts the
+ * coefficient-domain pursuit of a signal before a selection when
+ * reset_every > 0 selections were made since its last reset, or when
+ * reset_err_db < 0 and the estimate fell below it, 10 log10(E_k / E_out) <
+ * reset_err_db, E_out the energy at the last reset.  The reset synthesises
+ * all atoms selected so far (eq. idgtreal), takes the signal-domain
+ * residual r_out = x - x_hat, sets E_k = E_out = ||r_out||^2 (FP64) and
+ * re-analyses r_out; the pursuit then continues (stop tests first).  The
+ * atom list keeps growing across resets.  Both 0: no resets (default).
+ * Returns MP_EINVAL for reset_every < 0 or reset_err_db > 0.
+ */
+int mp_state_set_resets(mp_state* state, int64_t reset_every, double reset_err_db);
+
 /* copy the atom list of signal sig (host buffer of cap atoms); *n = count */
 int mp_get_atoms(const mp_state* state, int sig, mp_atom* out_host, int64_t cap, int64_t* n);
 /* energy estimates E_k after each atom (host doubles); *n = count */

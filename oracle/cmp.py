@@ -45,6 +45,10 @@ def lib():
         L.ora_mp_coef.restype = C.c_int
         L.ora_mp_plain.argtypes = common + [C.c_int64, C.c_double, C.c_int] + outs
         L.ora_mp_plain.restype = C.c_int
+        L.ora_mp_coef_reset.argtypes = common + [C.c_double, C.c_int64, C.c_double, C.c_int,
+                                                 C.c_int64, C.c_double] + outs + \
+            [C.POINTER(C.c_int64)]
+        L.ora_mp_coef_reset.restype = C.c_int
         _lib = L
     return _lib
 
@@ -112,7 +116,7 @@ class MPResult:
         return 10.0 * np.log10(self.E0 / self.E)
 
 
-def _run(fn, dicts, x, tail_args, kmax, extra_len):
+def _run(fn, dicts, x, tail_args, kmax, extra_len, resets=None):
     W, wl, a, M, gcat = _pack(dicts)
     x = np.ascontiguousarray(x, np.float64)
     cap = max(int(kmax), 1)
@@ -121,14 +125,20 @@ def _run(fn, dicts, x, tail_args, kmax, extra_len):
     ore, oim, oE, s1, s2 = (np.zeros(cap) for _ in range(5))
     na, st, E0 = C.c_int64(), C.c_int(), C.c_double()
     extra = np.zeros(extra_len) if extra_len else None
-    rc = fn(W, wl, a, M, gcat, x, x.size, *tail_args, od, om, on, ore, oim, oE, s1, s2,
+    args = [W, wl, a, M, gcat, x, x.size, *tail_args, od, om, on, ore, oim, oE, s1, s2,
             C.byref(na), C.byref(st), C.byref(E0),
-            extra.ctypes.data_as(C.c_void_p) if extra is not None else None)
+            extra.ctypes.data_as(C.c_void_p) if extra is not None else None]
+    nres = C.c_int64()
+    if resets is not None:
+        args.append(C.byref(nres))
+    rc = fn(*args)
     if rc != 0:
         raise RuntimeError("oracle failed (%d)" % rc)
     k = na.value
-    return MPResult(od[:k].copy(), om[:k].copy(), on[:k].copy(), ore[:k] + 1j * oim[:k],
-                    oE[:k].copy(), s1[:k].copy(), s2[:k].copy(), st.value, E0.value, extra)
+    res = MPResult(od[:k].copy(), om[:k].copy(), on[:k].copy(), ore[:k] + 1j * oim[:k],
+                   oE[:k].copy(), s1[:k].copy(), s2[:k].copy(), st.value, E0.value, extra)
+    res.n_resets = nres.value
+    return res
 
 
 def mp_coef(dicts, x, eps, kmax, snr_db, fullscan=False, planes=False):
@@ -148,6 +158,15 @@ def mp_coef(dicts, x, eps, kmax, snr_db, fullscan=False, planes=False):
             o += N * Mr
         res.extra = out
     return res
+
+
+def mp_coef_reset(dicts, x, eps, kmax, snr_db, reset_it=0, reset_db=0.0, fullscan=False):
+    """Alg. 2: coefficient-domain MP with resets (after reset_it selections
+    since the last reset, or once the estimate fell reset_db (< 0) dB below
+    the energy at the last reset)."""
+    return _run(lib().ora_mp_coef_reset, dicts, x,
+                [float(eps), int(kmax), float(snr_db), FLAG_FULLSCAN if fullscan else 0,
+                 int(reset_it), float(reset_db)], kmax, 0, resets=True)
 
 
 def mp_plain(dicts, x, kmax, snr_db, fullscan=False):

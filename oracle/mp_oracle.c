@@ -364,11 +364,41 @@ static void kernel_subtract(mpstate* s, const kern* K, int u, int v, int kk, int
     }
 }
 
+/* Alg. 2: approximate coefficient-domain MP with resets.  Before each
+ * selection, after the stop tests: when resets are enabled (reset_it > 0 or
+ * reset_db < 0) and at least one atom was selected since the last reset, and
+ * either reset_it selections have been made since it or the estimate has
+ * fallen by more than |reset_db| dB below the energy at the last reset,
+ * 10 log10(E_k / E_out) < reset_db, the residual is recomputed in the signal
+ * domain, r_out = x - (synthesis of all atoms so far), E_out = E_k =
+ * ||r_out||^2, the coefficients are re-analysed from r_out, and the stop
+ * tests are applied again.  reset_it = 0 and reset_db = 0 disable resets. */
+int ora_mp_coef_reset(int W, const int* wl, const int* a, const int* M, const double* gcat,
+                      const double* x, int64_t L, double eps, int64_t kmax, double target_db,
+                      int flags, int64_t reset_it, double reset_db,
+                      int32_t* o_dict, int32_t* o_m, int64_t* o_n, double* o_re, double* o_im,
+                      double* o_E, double* o_s1, double* o_s2,
+                      int64_t* n_atoms, int* stop_reason, double* E0_out, double* planes_out,
+                      int64_t* n_resets);
+
 int ora_mp_coef(int W, const int* wl, const int* a, const int* M, const double* gcat,
                 const double* x, int64_t L, double eps, int64_t kmax, double target_db, int flags,
                 int32_t* o_dict, int32_t* o_m, int64_t* o_n, double* o_re, double* o_im,
                 double* o_E, double* o_s1, double* o_s2,
                 int64_t* n_atoms, int* stop_reason, double* E0_out, double* planes_out) {
+    int64_t nr = 0;
+    return ora_mp_coef_reset(W, wl, a, M, gcat, x, L, eps, kmax, target_db, flags, 0, 0.0,
+                             o_dict, o_m, o_n, o_re, o_im, o_E, o_s1, o_s2, n_atoms, stop_reason,
+                             E0_out, planes_out, &nr);
+}
+
+int ora_mp_coef_reset(int W, const int* wl, const int* a, const int* M, const double* gcat,
+                      const double* x, int64_t L, double eps, int64_t kmax, double target_db,
+                      int flags, int64_t reset_it, double reset_db,
+                      int32_t* o_dict, int32_t* o_m, int64_t* o_n, double* o_re, double* o_im,
+                      double* o_E, double* o_s1, double* o_s2,
+                      int64_t* n_atoms, int* stop_reason, double* E0_out, double* planes_out,
+                      int64_t* n_resets) {
     mpstate s;
     if (state_init(&s, W, wl, a, M, gcat, L)) return -1;
 
@@ -409,9 +439,30 @@ int ora_mp_coef(int W, const int* wl, const int* a, const int* M, const double* 
     double thr = E0 * pow(10.0, -target_db / 10.0);
     int64_t k = 0;
     int stop = 0;
+    const int resets = reset_it > 0 || reset_db < 0.0;
+    double E_out = E0;
+    int64_t k_out = 0;
+    *n_resets = 0;
+    double* rout = resets ? (double*)malloc(sizeof(double) * (size_t)L) : NULL;
     for (;;) {
         stop = stop_before(E, thr, k, kmax);
         if (stop) break;
+        if (resets && k > k_out &&
+            ((reset_it > 0 && k - k_out >= reset_it) ||
+             (reset_db < 0.0 && 10.0 * log10(E / E_out) < reset_db))) {
+            /* r_out = x - D c for all atoms so far (eq. idgtreal) */
+            ora_synth(W, wl, a, M, gcat, k, o_dict, o_m, o_n, o_re, o_im, L, rout);
+            double Er = 0.0;
+            for (int64_t l = 0; l < L; ++l) {
+                rout[l] = x[l] - rout[l];
+                Er += rout[l] * rout[l];
+            }
+            E = E_out = Er;
+            k_out = k;
+            analyse_all(&s, rout);
+            (*n_resets)++;
+            continue;
+        }
         int u, kk;
         int64_t j;
         double sec;
@@ -471,6 +522,7 @@ int ora_mp_coef(int W, const int* wl, const int* a, const int* M, const double* 
     }
     for (int i = 0; i < W * W; ++i) { free(K[i].ent); free(K[i].full); }
     free(K);
+    free(rout);
     state_free(&s);
     return 0;
 }

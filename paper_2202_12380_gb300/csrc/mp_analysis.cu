@@ -32,7 +32,8 @@ __device__ __forceinline__ int find_sig(const long long* prefix, int nsig, long 
 __global__ void __launch_bounds__(256) k_analysis_sgemm(const float* __restrict__ A, int Kp, int w,
                                                         int a, int Mrp, int nsig,
                                                         const long long* __restrict__ tprefix,
-                                                        const DevSig* __restrict__ sigs, int dict) {
+                                                        const DevSig* __restrict__ sigs, int dict,
+                                                        int flagged) {
     __shared__ __align__(16) float As[BK][BM];
     __shared__ __align__(16) float Bs[BK][BN];
     const int tid = threadIdx.x;
@@ -40,9 +41,10 @@ __global__ void __launch_bounds__(256) k_analysis_sgemm(const float* __restrict_
     const long long gt = blockIdx.x;
     const int s = find_sig(tprefix, nsig, gt);
     const DevSig& S = sigs[s];
+    if (flagged && !S.reanalyze) return;
     const long long N = S.N[dict];
     const long long L = S.L;
-    const float* __restrict__ x = S.x;
+    const float* __restrict__ x = S.use_r ? S.r : S.x;
     const long long n0 = (gt - tprefix[s]) * BN;
     const int r0 = blockIdx.y * BM;
 
@@ -140,6 +142,11 @@ __global__ void __launch_bounds__(1024) k_energy(DevSig* sigs) {
             S.k = 0;
             S.stop = 0;
             S.timed_out = 0;
+            S.k_out = 0;
+            S.E_out = v;
+            S.reset_pending = 0;
+            S.reanalyze = 0;
+            S.use_r = 0;
         }
     }
 }
@@ -147,12 +154,14 @@ __global__ void __launch_bounds__(1024) k_energy(DevSig* sigs) {
 // level 0 (per 32-bin chunk) and level 1 (per frame) of dictionary `dict`,
 // one warp per frame
 __global__ void k_tree_build(DevPlan P, const DevSig* __restrict__ sigs, int nsig,
-                             const long long* __restrict__ fprefix, long long total, int dict) {
+                             const long long* __restrict__ fprefix, long long total, int dict,
+                             int flagged) {
     long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (gw >= total) return;
     const int lane = threadIdx.x & 31;
     const int s = find_sig(fprefix, nsig, gw);
     const DevSig& S = sigs[s];
+    if (flagged && !S.reanalyze) return;
     const long long n = gw - fprefix[s];
     const DevDict& D = P.d[dict];
     const float2* row = S.plane[dict] + n * D.Mrp;
@@ -176,7 +185,8 @@ __global__ void k_tree_build(DevPlan P, const DevSig* __restrict__ sigs, int nsi
 // level 2: groups of 2^gshift frames (signals whose frames exceed the
 // on-chip top level), one warp per group
 __global__ void k_group_build(const DevSig* __restrict__ sigs, int nsig,
-                              const int* __restrict__ gprefix, long long total, int W) {
+                              const int* __restrict__ gprefix, long long total, int W,
+                              int flagged) {
     long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (gw >= total) return;
     const int lane = threadIdx.x & 31;
@@ -186,6 +196,7 @@ __global__ void k_group_build(const DevSig* __restrict__ sigs, int nsig,
         if (gprefix[mid] <= gw) lo = mid; else hi = mid - 1;
     }
     const DevSig& S = sigs[lo];
+    if (flagged && !S.reanalyze) return;
     const int g = (int)(gw - gprefix[lo]);
     int w = 0;
     while (w + 1 < W && S.tbase[w + 1] <= g) ++w;
@@ -202,14 +213,51 @@ __global__ void k_group_build(const DevSig* __restrict__ sigs, int nsig,
     if (lane == 0) S.grp[g] = r;
 }
 
+// reset pass, one block per signal: r = x - y and E = E_out = ||r||^2
+// (FP64, fixed order) for the flagged signals
+__global__ void __launch_bounds__(1024) k_reset_residual(DevSig* sigs) {
+    DevSig& S = sigs[blockIdx.x];
+    if (!S.reanalyze) return;
+    double acc = 0.0;
+    for (long long l = threadIdx.x; l < S.L; l += blockDim.x) {
+        const float d = S.x[l] - S.y[l];
+        S.r[l] = d;
+        acc = fma((double)d, (double)d, acc);
+    }
+    __shared__ double red[32];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+        if (threadIdx.x == 0) {
+            S.E = v;
+            S.E_out = v;
+            S.k_out = S.k;
+            S.reset_pending = 0;
+            S.use_r = 1;
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_analysis_sgemm(const float* A, int Arows, int Kp, int w_len, int a, int Mrp,
                                   int nsig, const long long* d_tile_prefix, const DevSig* d_sigs,
-                                  int dict, long long total_frame_tiles, cudaStream_t st) {
+                                  int dict, long long total_frame_tiles, cudaStream_t st,
+                                  int flagged) {
     if (total_frame_tiles <= 0) return cudaSuccess;
     dim3 grid((unsigned)total_frame_tiles, (unsigned)(Arows / BM));
-    k_analysis_sgemm<<<grid, 256, 0, st>>>(A, Kp, w_len, a, Mrp, nsig, d_tile_prefix, d_sigs, dict);
+    k_analysis_sgemm<<<grid, 256, 0, st>>>(A, Kp, w_len, a, Mrp, nsig, d_tile_prefix, d_sigs, dict,
+                                           flagged);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_residual(DevSig* d_sigs, int nsig, cudaStream_t st) {
+    k_reset_residual<<<nsig, 1024, 0, st>>>(d_sigs);
     return cudaGetLastError();
 }
 
@@ -220,20 +268,20 @@ cudaError_t launch_energy(const DevSig* d_sigs, int nsig, double*, int, cudaStre
 
 cudaError_t launch_tree_build(const DevPlan& P, const DevSig* d_sigs, int nsig,
                               const long long* d_frame_prefix, long long total_frames, int dict,
-                              cudaStream_t st) {
+                              cudaStream_t st, int flagged) {
     if (total_frames <= 0) return cudaSuccess;
     const int wpb = 8;
     k_tree_build<<<(unsigned)((total_frames + wpb - 1) / wpb), wpb * 32, 0, st>>>(
-        P, d_sigs, nsig, d_frame_prefix, total_frames, dict);
+        P, d_sigs, nsig, d_frame_prefix, total_frames, dict, flagged);
     return cudaGetLastError();
 }
 
 cudaError_t launch_group_build(const DevSig* d_sigs, int nsig, const int* d_group_prefix,
-                               long long total_groups, int W, cudaStream_t st) {
+                               long long total_groups, int W, cudaStream_t st, int flagged) {
     if (total_groups <= 0) return cudaSuccess;
     const int wpb = 8;
     k_group_build<<<(unsigned)((total_groups + wpb - 1) / wpb), wpb * 32, 0, st>>>(
-        d_sigs, nsig, d_group_prefix, total_groups, W);
+        d_sigs, nsig, d_group_prefix, total_groups, W, flagged);
     return cudaGetLastError();
 }
 

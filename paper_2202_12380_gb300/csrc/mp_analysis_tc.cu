@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(128, 1)
                   const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
                   int Kp, int a, int Mrp, int nsig, const long long* __restrict__ tprefix,
                   const int* __restrict__ brow, const DevSig* __restrict__ sigs, int dict,
-                  int* __restrict__ err) {
+                  int* __restrict__ err, int flagged) {
     extern __shared__ unsigned char smem_raw[];
     const unsigned raw = smem_u32(smem_raw);
     const unsigned base = (raw + 1023u) & ~1023u;
@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(128, 1)
     const long long gt = blockIdx.x;
     const int s = find_tile_sig(tprefix, nsig, gt);
     const DevSig& S = sigs[s];
+    if (flagged && !S.reanalyze) return;  // uniform per CTA, before any barrier
     const long long N = S.N[dict];
     const int n0 = (int)((gt - tprefix[s]) * TBN);
     const int r0 = blockIdx.y * TBM;
@@ -281,12 +282,15 @@ __global__ void k_split_rows(const float* __restrict__ src, int rows, int cols, 
 // padded signal segment: seg[j] = x((j - pad) mod L) for j < seg_len
 __global__ void k_split_segment(const DevSig* __restrict__ sigs, const long long* __restrict__ seg_off,
                                 const long long* __restrict__ seg_len, int pad,
-                                __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+                                __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                                int flagged) {
     const DevSig& S = sigs[blockIdx.y];
+    if (flagged && !S.reanalyze) return;
+    const float* xin = S.use_r ? S.r : S.x;
     const long long off = seg_off[blockIdx.y], len = seg_len[blockIdx.y];
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < len;
          j += (long long)gridDim.x * blockDim.x) {
-        const float v = S.x[lmod(j - pad, S.L)];
+        const float v = xin[lmod(j - pad, S.L)];
         const __nv_bfloat16 h = __float2bfloat16_rn(v);
         hi[off + j] = h;
         lo[off + j] = __float2bfloat16_rn(v - __bfloat162float(h));
@@ -307,17 +311,17 @@ cudaError_t launch_split_rows(const float* src, int rows, int cols, int src_ld, 
 
 cudaError_t launch_split_segments(const DevSig* d_sigs, int nsig, const long long* seg_off,
                                   const long long* seg_len, int pad, void* hi, void* lo,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, int flagged) {
     dim3 grid(256, (unsigned)nsig);
     k_split_segment<<<grid, 256, 0, st>>>(d_sigs, seg_off, seg_len, pad, (__nv_bfloat16*)hi,
-                                          (__nv_bfloat16*)lo);
+                                          (__nv_bfloat16*)lo, flagged);
     return cudaGetLastError();
 }
 
 cudaError_t launch_analysis_tc(const void* tmaps /* 4 CUtensorMap */, int Arows, int Kp, int a,
                                int Mrp, int nsig, const long long* d_tile_prefix, const int* d_brow,
                                const DevSig* d_sigs, int dict, long long total_tiles, int* d_err,
-                               cudaStream_t st) {
+                               cudaStream_t st, int flagged) {
     if (total_tiles <= 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_analysis_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          TC_SMEM);
@@ -325,7 +329,7 @@ cudaError_t launch_analysis_tc(const void* tmaps /* 4 CUtensorMap */, int Arows,
     const CUtensorMap* m = static_cast<const CUtensorMap*>(tmaps);
     dim3 grid((unsigned)total_tiles, (unsigned)(Arows / TBM));
     k_analysis_tc<<<grid, 128, TC_SMEM, st>>>(m[0], m[1], m[2], m[3], Kp, a, Mrp, nsig,
-                                              d_tile_prefix, d_brow, d_sigs, dict, d_err);
+                                              d_tile_prefix, d_brow, d_sigs, dict, d_err, flagged);
     return cudaGetLastError();
 }
 

@@ -51,6 +51,8 @@ struct mp_state {
     double* d_errs;
     double* d_scalar;
     double time_limit_s;
+    long long reset_it;      // resets (Alg. 2): selections per reset, 0 = off
+    double reset_db;         // resets once 10 log10(E/E_out) < reset_db (< 0), 0 = off
     // split-BF16 analysis: padded BF16 signal segments and per-dictionary views
     void* d_xhi;
     void* d_xlo;
@@ -158,11 +160,14 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
     s->d_scalar = nullptr;
     s->cap = 0;
     s->time_limit_s = 0.0;
+    s->reset_it = 0;
+    s->reset_db = 0.0;
     s->Tmax = 1;
     const int W = p->W;
     // layout of every signal inside one pool
     size_t off = 0;
-    std::vector<size_t> o_plane(B * W), o_l0(B * W), o_l1(B * W), o_grp(B), o_x(B);
+    std::vector<size_t> o_plane(B * W), o_l0(B * W), o_l1(B * W), o_grp(B), o_x(B), o_r(B),
+        o_y(B);
     for (int b = 0; b < B; ++b) {
         DevSig& S = s->hs[b];
         memset(&S, 0, sizeof(S));
@@ -205,6 +210,10 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
         if (gs > 0) off = align256(off + sizeof(Entry) * tb);
         o_x[b] = off;
         off = align256(off + sizeof(float) * L[b]);
+        o_r[b] = off;
+        off = align256(off + sizeof(float) * L[b]);
+        o_y[b] = off;
+        off = align256(off + sizeof(float) * L[b]);
     }
     cudaError_t e = cudaMalloc(&s->pool, std::max<size_t>(off, 256));
     if (e != cudaSuccess) {
@@ -221,6 +230,8 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
         }
         S.grp = S.gshift > 0 ? (Entry*)(base + o_grp[b]) : nullptr;
         S.x = (const float*)(base + o_x[b]);
+        S.r = (float*)(base + o_r[b]);
+        S.y = (float*)(base + o_y[b]);
     }
     // zero the pool once so padding bins are zero
     cudaStream_t st = p->stream;
@@ -328,6 +339,8 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
     return MP_OK;
 }
 
+int analysis_pass(mp_state* s, int flagged);
+
 int analyze_impl(const mp_plan* p, mp_state** state, int B, const float* const* x,
                  const int64_t* L, cudaMemcpyKind kind) {
     if (!p || !state || !x) {
@@ -357,10 +370,23 @@ int analyze_impl(const mp_plan* p, mp_state** state, int B, const float* const* 
     for (int b = 0; b < B; ++b)
         CKR(cudaMemcpyAsync((void*)s->hs[b].x, x[b], sizeof(float) * L[b], kind, st));
     CKR(launch_energy(s->d_sigs, B, nullptr, 0, st));
+    rc = analysis_pass(s, 0);
+    if (rc) return rc;
+    if (kind == cudaMemcpyHostToDevice) CKR(cudaStreamSynchronize(st));
+    *state = s;
+    return MP_OK;
+}
+
+// coefficient planes and max trees of every signal (flagged = 0) or of the
+// signals flagged for a reset pass (flagged = 1)
+int analysis_pass(mp_state* s, int flagged) {
+    const mp_plan* p = s->plan;
+    const int B = s->B;
+    cudaStream_t st = p->stream;
     const bool tc = (p->flags & MP_ANALYSIS_BF16X3) != 0;
     if (tc)
         CKR(launch_split_segments(s->d_sigs, B, s->d_seg, s->d_seg + B, s->seg_pad, s->d_xhi,
-                                  s->d_xlo, st));
+                                  s->d_xlo, st, flagged));
     for (int w = 0; w < p->W; ++w) {
         const DevDict& D = p->dp.d[w];
         if (tc) {
@@ -371,14 +397,16 @@ int analyze_impl(const mp_plan* p, mp_state** state, int B, const float* const* 
             memcpy(maps[3], s->tmB[w][1], 128);
             CKR(launch_analysis_tc(maps, p->Arows[w], p->Kp64[w], D.a, D.Mrp, B, s->d_tc_prefix[w],
                                    s->d_brow + (size_t)w * B, s->d_sigs, w, s->total_tc_tiles[w],
-                                   s->d_err, st));
+                                   s->d_err, st, flagged));
         } else {
             CKR(launch_analysis_sgemm(p->d_A[w], p->Arows[w], p->Akp[w], D.wlen, D.a, D.Mrp, B,
-                                      s->d_tile_prefix[w], s->d_sigs, w, s->total_tiles[w], st));
+                                      s->d_tile_prefix[w], s->d_sigs, w, s->total_tiles[w], st,
+                                      flagged));
         }
-        CKR(launch_tree_build(p->dp, s->d_sigs, B, s->d_frame_prefix[w], s->total_frames[w], w, st));
+        CKR(launch_tree_build(p->dp, s->d_sigs, B, s->d_frame_prefix[w], s->total_frames[w], w, st,
+                              flagged));
     }
-    CKR(launch_group_build(s->d_sigs, B, s->d_group_prefix, s->total_groups, p->W, st));
+    CKR(launch_group_build(s->d_sigs, B, s->d_group_prefix, s->total_groups, p->W, st, flagged));
     if (tc) {
         // the tensor-core kernel bounds its waits; report an expired wait
         int err = 0;
@@ -389,8 +417,6 @@ int analyze_impl(const mp_plan* p, mp_state** state, int B, const float* const* 
             return MP_ETIMEOUT;
         }
     }
-    if (kind == cudaMemcpyHostToDevice) CKR(cudaStreamSynchronize(st));
-    *state = s;
     return MP_OK;
 }
 
@@ -433,11 +459,17 @@ int ensure_capacity(mp_state* s, long long kmax) {
     return MP_OK;
 }
 
-int read_status(mp_state* s, int64_t* n_atoms, int* stop, double* snr, bool* timed_out) {
+int read_status(mp_state* s, int64_t* n_atoms, int* stop, double* snr, bool* timed_out,
+                std::vector<int>* resets = nullptr) {
     std::vector<DevSig> dv(s->B);
     CKR(cudaMemcpyAsync(dv.data(), s->d_sigs, sizeof(DevSig) * s->B, cudaMemcpyDeviceToHost,
                         s->plan->stream));
     CKR(cudaStreamSynchronize(s->plan->stream));
+    if (resets) {
+        resets->clear();
+        for (int b = 0; b < s->B; ++b)
+            if (dv[b].reset_pending) resets->push_back(b);
+    }
     bool to = false;
     for (int b = 0; b < s->B; ++b) {
         if (n_atoms) n_atoms[b] = dv[b].k;
@@ -497,8 +529,30 @@ extern "C" int mp_run_async(mp_state* s, int64_t K_max, double target_snr_db) {
     const double thr_scale = std::pow(10.0, -target_snr_db / 10.0);
     const long long budget =
         s->time_limit_s > 0 ? (long long)std::min(s->time_limit_s * 1e9, 9e18) : 0LL;
+    const double reset_scale = s->reset_db < 0.0 ? std::pow(10.0, s->reset_db / 10.0) : 0.0;
     CKR(launch_mp_loop(s->plan->dp, s->d_sigs, s->d_order, s->B, K_max, thr_scale, budget, s->smem,
-                       s->threads, s->cs, s->plan->stream));
+                       s->threads, s->cs, s->plan->stream, s->reset_it, reset_scale));
+    return MP_OK;
+}
+
+// Alg. 2 reset pass for the listed signals: synthesise all atoms so far,
+// r = x - y, E = E_out = ||r||^2, re-analyse r
+static int reset_pass(mp_state* s, const std::vector<int>& sigs) {
+    cudaStream_t st = s->plan->stream;
+    const int one = 1;
+    for (int b : sigs) {
+        CKR(launch_synth(s->plan->dp, s->d_sigs + b, 0, s->hs[b].y, s->L[b], st));
+        CKR(cudaMemcpyAsync((char*)(s->d_sigs + b) + offsetof(DevSig, reanalyze), &one, sizeof(int),
+                            cudaMemcpyHostToDevice, st));
+    }
+    CKR(launch_reset_residual(s->d_sigs, s->B, st));
+    int rc = analysis_pass(s, 1);
+    if (rc) return rc;
+    const int zero = 0;
+    for (int b : sigs)
+        CKR(cudaMemcpyAsync((char*)(s->d_sigs + b) + offsetof(DevSig, reanalyze), &zero,
+                            sizeof(int), cudaMemcpyHostToDevice, st));
+    CKR(cudaStreamSynchronize(st));
     return MP_OK;
 }
 
@@ -519,9 +573,29 @@ extern "C" int mp_get_status(mp_state* s, int64_t* n_atoms, int* stop, double* s
 
 extern "C" int mp_run(mp_state* s, int64_t K_max, double target_snr_db, int64_t* n_atoms,
                       int* stop_reason, double* final_snr_db) {
-    int rc = mp_run_async(s, K_max, target_snr_db);
-    if (rc) return rc;
+    for (;;) {
+        int rc = mp_run_async(s, K_max, target_snr_db);
+        if (rc) return rc;
+        if (s->reset_it <= 0 && s->reset_db >= 0.0) break;
+        std::vector<int> pend;
+        bool to = false;
+        rc = read_status(s, nullptr, nullptr, nullptr, &to, &pend);
+        if (rc) return rc;
+        if (pend.empty() || to) break;
+        rc = reset_pass(s, pend);
+        if (rc) return rc;
+    }
     return mp_get_status(s, n_atoms, stop_reason, final_snr_db);
+}
+
+extern "C" int mp_state_set_resets(mp_state* s, int64_t reset_every, double reset_err_db) {
+    if (!s || reset_every < 0 || !(reset_err_db <= 0.0)) {
+        mpg_set_error("mp_state_set_resets: need reset_every >= 0 and reset_err_db <= 0");
+        return MP_EINVAL;
+    }
+    s->reset_it = reset_every;
+    s->reset_db = reset_err_db;
+    return MP_OK;
 }
 
 extern "C" int mp_get_atoms(const mp_state* s, int sig, mp_atom* out, int64_t cap, int64_t* n) {

@@ -96,23 +96,40 @@ struct DevSig {
     double E0;
     int stop;
     int timed_out;
+    // resets (Alg. 2): residual and synthesis buffers, the last reset's
+    // atom count and energy, and the hand-over flags between launches
+    float* r;
+    float* y;
+    long long k_out;
+    double E_out;
+    int reset_pending;  // the MP launch stopped for a reset
+    int reanalyze;      // analysis kernels act on this signal (reset pass)
+    int use_r;          // the analysis reads r instead of x
+    int pad2;
 };
 
 // ---- host launchers implemented in the .cu files -------------------------
 // analysis: rho = A * frames for dictionary w of the listed signals
+// flagged: act only on signals whose `reanalyze` flag is set (reset pass)
 cudaError_t launch_analysis_sgemm(const float* A, int Arows, int Kp, int w_len, int a, int Mrp,
                                   int nsig, const long long* d_tile_prefix, const DevSig* d_sigs,
-                                  int dict, long long total_frame_tiles, cudaStream_t st);
+                                  int dict, long long total_frame_tiles, cudaStream_t st,
+                                  int flagged = 0);
 cudaError_t launch_energy(const DevSig* d_sigs, int nsig, double* d_partials, int nparts,
                           cudaStream_t st);
+// reset pass: r = x - y for flagged signals, then E = E_out = ||r||^2
+cudaError_t launch_reset_residual(DevSig* d_sigs, int nsig, cudaStream_t st);
 cudaError_t launch_tree_build(const DevPlan& P, const DevSig* d_sigs, int nsig,
                               const long long* d_frame_prefix, long long total_frames, int dict,
-                              cudaStream_t st);
+                              cudaStream_t st, int flagged = 0);
 cudaError_t launch_group_build(const DevSig* d_sigs, int nsig, const int* d_group_prefix,
-                               long long total_groups, int W, cudaStream_t st);
+                               long long total_groups, int W, cudaStream_t st, int flagged = 0);
+// reset_it > 0: reset after that many selections since the last reset;
+// reset_scale > 0: reset once E < E_out reset_scale
 cudaError_t launch_mp_loop(const DevPlan& P, DevSig* d_sigs, const int* d_order, int nsig,
                            long long kmax, double thr_scale, long long budget_ns, size_t smem,
-                           int threads, int cs, cudaStream_t st);
+                           int threads, int cs, cudaStream_t st, long long reset_it = 0,
+                           double reset_scale = 0.0);
 void mp_loop_shape(const DevPlan& P, const DevSig* hs, int B, int num_sms, int* threads, int* cs,
                    size_t* smem);
 cudaError_t launch_synth(const DevPlan& P, const DevSig* d_sig, long long natoms, float* y,
@@ -126,11 +143,11 @@ cudaError_t launch_split_rows(const float* src, int rows, int cols, int src_ld, 
                               void* hi, void* lo, cudaStream_t st);
 cudaError_t launch_split_segments(const DevSig* d_sigs, int nsig, const long long* seg_off,
                                   const long long* seg_len, int pad, void* hi, void* lo,
-                                  cudaStream_t st);
+                                  cudaStream_t st, int flagged = 0);
 cudaError_t launch_analysis_tc(const void* tmaps, int Arows, int Kp, int a, int Mrp, int nsig,
                                const long long* d_tile_prefix, const int* d_brow,
                                const DevSig* d_sigs, int dict, long long total_tiles, int* d_err,
-                               cudaStream_t st);
+                               cudaStream_t st, int flagged = 0);
 // encodes a 2-D BF16 tensor map with a 64 x 128 box and 128-byte swizzle
 // (mp_plan.cu); returns false on failure
 bool encode_bf16_map(void* map, const void* base, unsigned long long inner,

@@ -281,7 +281,8 @@ __device__ __forceinline__ bool chunk_touched(const DictJob& J, int c) {
 template <int NT>
 __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     k_mp_loop(DevPlan P, DevSig* __restrict__ sigs, const int* __restrict__ order,
-              long long kmax, double thr_scale, long long budget_ns, int CS) {
+              long long kmax, double thr_scale, long long budget_ns, int CS, long long reset_it,
+              double reset_scale) {
     namespace cg = cooperative_groups;
     constexpr int NWARPS = NT / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -353,6 +354,11 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     double E = S.E;
     const double E0 = S.E0;
     const double thr = E0 * thr_scale;
+    // resets (Alg. 2): stop the launch for a reset pass once reset_it atoms
+    // were selected since the last reset or E dropped below E_out reset_scale
+    const bool resets = reset_it > 0 || reset_scale > 0.0;
+    const long long k_out = S.k_out;
+    const double E_out = S.E_out;
     const unsigned long long t_start = gtimer();
     const float2* __restrict__ tiles = P.tiles;
     const unsigned xbytes = (unsigned)(CS * sizeof(Entry)) + (budget_ns > 0 ? 16u : 0u);
@@ -363,6 +369,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         else if (E <= 0.0) s0 = MP_STOP_NEGENERGY;
         else if (E <= thr) s0 = MP_STOP_SNR;
         else if (k >= kmax) s0 = MP_STOP_KMAX;
+        else if (resets && k > k_out &&
+                 ((reset_it > 0 && k - k_out >= reset_it) ||
+                  (reset_scale > 0.0 && E < E_out * reset_scale)))
+            s0 = -3;
         sstop[k & 1] = s0;
     }
     // every CTA's barriers are initialised before anyone sends
@@ -496,6 +506,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
             if (E <= 0.0) s1 = MP_STOP_NEGENERGY;
             else if (E <= thr) s1 = MP_STOP_SNR;
             else if (k + 1 >= kmax) s1 = MP_STOP_KMAX;
+            else if (resets && ((reset_it > 0 && k + 1 - k_out >= reset_it) ||
+                                (reset_scale > 0.0 && E < E_out * reset_scale)))
+                s1 = -3;  // reset pass (Alg. 2) before the next selection
             sstop[(k + 1) & 1] = s1;
         }
         ++k;
@@ -663,9 +676,14 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     if (tid == KEEPER && rank == 0) {
         Sg.k = k;
         Sg.E = E;
+        Sg.reset_pending = 0;
         if (stop > 0) {
             Sg.stop = stop;
             Sg.timed_out = 0;
+        } else if (stop == -3) {
+            Sg.stop = 0;
+            Sg.timed_out = 0;
+            Sg.reset_pending = 1;
         } else {
             Sg.stop = 0;
             Sg.timed_out = 1;
@@ -675,7 +693,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
 
 template <int NT>
 cudaError_t launch_nt(const DevPlan& P, DevSig* d_sigs, const int* d_order, int nsig, long long kmax,
-                      double thr_scale, long long budget_ns, size_t smem, int cs, cudaStream_t st) {
+                      double thr_scale, long long budget_ns, size_t smem, int cs, cudaStream_t st,
+                      long long reset_it, double reset_scale) {
     cudaError_t e = cudaFuncSetAttribute(k_mp_loop<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -695,7 +714,8 @@ cudaError_t launch_nt(const DevPlan& P, DevSig* d_sigs, const int* d_order, int 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_mp_loop<NT>, P, d_sigs, d_order, kmax, thr_scale, budget_ns, cs);
+    e = cudaLaunchKernelEx(&cfg, k_mp_loop<NT>, P, d_sigs, d_order, kmax, thr_scale, budget_ns, cs,
+                           reset_it, reset_scale);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -801,15 +821,20 @@ void mp_loop_shape(const DevPlan& P, const DevSig* hs, int B, int num_sms, int* 
 
 cudaError_t launch_mp_loop(const DevPlan& P, DevSig* d_sigs, const int* d_order, int nsig,
                            long long kmax, double thr_scale, long long budget_ns, size_t smem,
-                           int threads, int cs, cudaStream_t st) {
+                           int threads, int cs, cudaStream_t st, long long reset_it,
+                           double reset_scale) {
     if (nsig <= 0) return cudaSuccess;
+#define MPG_LAUNCH(NTV)                                                                        \
+    launch_nt<NTV>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, cs, st, reset_it, \
+                   reset_scale)
     switch (threads) {
-        case 1024: return launch_nt<1024>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, cs, st);
-        case 512: return launch_nt<512>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, cs, st);
-        case 256: return launch_nt<256>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, cs, st);
-        case 128: return launch_nt<128>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, cs, st);
+        case 1024: return MPG_LAUNCH(1024);
+        case 512: return MPG_LAUNCH(512);
+        case 256: return MPG_LAUNCH(256);
+        case 128: return MPG_LAUNCH(128);
         default: return cudaErrorInvalidValue;
     }
+#undef MPG_LAUNCH
 }
 
 }  // namespace mpg

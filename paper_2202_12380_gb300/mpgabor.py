@@ -29,7 +29,7 @@ EXPORTS = [
     "mp_plan_tile_info", "mp_plan_tile", "mp_plan_gamma", "mp_analyze", "mp_analyze_host",
     "mp_state_coefficients", "mp_run", "mp_run_async", "mp_get_status", "mp_state_set_time_limit",
     "mp_get_atoms", "mp_get_errors", "mp_synthesize", "mp_state_destroy", "mp_last_error",
-    "mp_decompose_static",
+    "mp_decompose_static", "mp_state_set_resets",
 ]
 
 _lib = None
@@ -77,6 +77,7 @@ def lib():
         "mp_state_destroy": ([vp], None),
         "mp_last_error": ([], C.c_char_p),
         "mp_decompose_static": ([vp, vp, i64, i64, dbl, vp, vp, P(i64), P(i32), P(dbl)], i32),
+        "mp_state_set_resets": ([vp, i64, dbl], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -276,6 +277,12 @@ def mp_get_status(state: State):
 
 def mp_state_set_time_limit(state: State, seconds: float):
     _check(lib().mp_state_set_time_limit(state.handle, float(seconds)))
+
+
+def mp_state_set_resets(state: State, reset_every: int = 0, reset_err_db: float = 0.0):
+    """Alg. 2 resets: after reset_every selections since the last reset, or
+    once 10 log10(E_k / E_out) < reset_err_db (< 0); 0 disables either."""
+    _check(lib().mp_state_set_resets(state.handle, int(reset_every), float(reset_err_db)))
 
 
 def mp_get_atoms(state: State, sig: int, cap: int | None = None):

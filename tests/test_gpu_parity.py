@@ -382,3 +382,42 @@ def test_bf16x3_rejects_incompatible_hops():
     with pytest.raises(mg.MPError) as ei:
         _plan([(inputs.blackman(64), 16, 64)], 1e-4, mg.MP_ANALYSIS_BF16X3)
     assert ei.value.code == mg.MP_EINVAL
+
+
+# ------------------------------------------------------------ resets (Alg. 2)
+
+@pytest.mark.parametrize("mode", ["every", "db"])
+def test_resets_match_oracle(mode):
+    """Alg. 2 on the GPU against the oracle's reset loop, with a coarse
+    kernel threshold so that resets change the result."""
+    L, dicts = 16384, [(inputs.blackman(w), w // 4, w) for w in (128, 256, 512)]
+    x = inputs.as_f32(inputs.mixture(L, 35, fs=16000.0))
+    eps, K = 1e-2, 400
+    it, db = (60, 0.0) if mode == "every" else (0, -3.0)
+    ref = cmp.mp_coef_reset(dicts, x.astype(np.float64), eps, K, 200.0, reset_it=it, reset_db=db)
+    assert ref.n_resets > 0
+    plan = _plan(dicts, eps)
+    st = mg.mp_analyze(plan, [torch.from_numpy(x).cuda()])
+    mg.mp_state_set_resets(st, it, db)
+    n, stop, q = mg.mp_run(st, K, 200.0)
+    atoms, errs = mg.mp_get_atoms(st, 0), mg.mp_get_errors(st, 0)
+    E0 = float(np.sum(x.astype(np.float64) ** 2))
+    r = compare(atoms, errs, E0, ref, min_checked=60)
+    print(mode, ref.n_resets, r)
+
+
+def test_resets_batched_only_flagged_signals_reanalysed():
+    """In a batch, the reset pass re-analyses only the signals that asked for
+    it; every signal still matches its own oracle run."""
+    dicts = [(inputs.blackman(w), w // 4, w) for w in (128, 256)]
+    lens = [4096, 8192, 6144]
+    xs = [inputs.as_f32(inputs.mixture(L, 40 + i, fs=16000.0)) for i, L in enumerate(lens)]
+    eps, K = 1e-2, 150
+    plan = _plan(dicts, eps)
+    st = mg.mp_analyze(plan, [torch.from_numpy(x).cuda() for x in xs])
+    mg.mp_state_set_resets(st, 0, -2.0)
+    mg.mp_run(st, K, 200.0)
+    for b, x in enumerate(xs):
+        ref = cmp.mp_coef_reset(dicts, x.astype(np.float64), eps, K, 200.0, reset_db=-2.0)
+        atoms, errs = mg.mp_get_atoms(st, b), mg.mp_get_errors(st, b)
+        compare(atoms, errs, float(np.sum(x.astype(np.float64) ** 2)), ref, min_checked=20)

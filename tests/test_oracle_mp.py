@@ -148,3 +148,85 @@ def test_stop_rules():
     # without a target the estimate eventually goes negative (Sec. 6.1 rule)
     big = cmp.mp_coef(dicts, x, 5e-2, 200000, 400.0)
     assert big.stop == cmp.STOP_NEGENERGY and big.E[-1] <= 0 and np.all(big.E[:-1] > 0)
+
+
+# ------------------------------------------------------------- resets -----
+
+def test_reset_every_atom_is_plain_mp():
+    """Alg. 2 with a reset before every selection re-analyses the exact
+    residual each time, so even with a coarse threshold it reproduces plain
+    MP's selections.  Coefficients differ only where the exact <d, conj d>
+    is below the threshold and taken as zero (Sec. 5.2), i.e. by at most
+    about |gamma| <= eps relative."""
+    L = 1024
+    dicts = [(inputs.blackman(w), w // 4, w) for w in (64, 128)]
+    x = inputs.mixture(L, 15, fs=8000.0)
+    K = 80
+    plain = cmp.mp_plain(dicts, x, K, 400.0)
+    rs = cmp.mp_coef_reset(dicts, x, 1e-2, K, 400.0, reset_it=1)
+    assert rs.n_resets == K - 1
+    assert np.array_equal(plain.dict, rs.dict) and np.array_equal(plain.m, rs.m)
+    assert np.array_equal(plain.n, rs.n)
+    rel = np.abs(plain.c - rs.c) / np.abs(plain.c)
+    assert np.max(rel) < 2 * 1e-2
+    assert np.median(rel) < 1e-12  # interior atoms: gamma is zero in both
+    assert np.max(np.abs(plain.E - rs.E)) < 1e-3 * plain.E0
+
+
+def test_reset_energy_is_true_residual_energy():
+    """Right after a reset the estimate restarts from the exact residual
+    energy: E_k (after atom k, the first atom of an epoch) equals
+    ||x - synthesis of atoms 0..k-1||^2 minus that atom's energy drop."""
+    L = 2048
+    dicts = [(inputs.blackman(w), w // 4, w) for w in (64, 256)]
+    x = inputs.mixture(L, 16, fs=8000.0)
+    K = 300
+    rs = cmp.mp_coef_reset(dicts, x, 1e-2, K, 400.0, reset_it=50)
+    assert rs.n_resets == (K - 1) // 50
+    no = cmp.mp_coef(dicts, x, 1e-2, K, 400.0)
+
+    class S:
+        pass
+
+    for kr in range(50, K, 50):
+        s = S()
+        s.dict, s.m, s.n, s.c = rs.dict[:kr], rs.m[:kr], rs.n[:kr], rs.c[:kr]
+        r = x - cmp.synth(dicts, s, L)
+        s2 = S()
+        s2.dict, s2.m, s2.n, s2.c = rs.dict[:kr + 1], rs.m[:kr + 1], rs.n[:kr + 1], rs.c[:kr + 1]
+        r2 = x - cmp.synth(dicts, s2, L)
+        # the estimate after the epoch's first atom is exact up to the
+        # truncation of that one atom's projection
+        assert abs(rs.E[kr] - float(r2 @ r2)) < 1e-6 * rs.E0
+        assert float(r @ r) > float(r2 @ r2)
+    # without resets the estimate drifts away from the true energy
+    s3 = S()
+    s3.dict, s3.m, s3.n, s3.c = no.dict, no.m, no.n, no.c
+    r3 = x - cmp.synth(dicts, s3, L)
+    assert abs(no.E[-1] - float(r3 @ r3)) > abs(rs.E[-1] - float((x - cmp.synth(dicts, rs, L)) @
+                                                                  (x - cmp.synth(dicts, rs, L))))
+
+
+def test_resets_restore_convergence_with_coarse_threshold():
+    """With a coarse kernel threshold the estimate drifts from the true
+    error; resets keep the true residual decreasing to the target."""
+    L = 2048
+    dicts = [(inputs.blackman(w), w // 4, w) for w in (64, 256)]
+    x = inputs.mixture(L, 17, fs=8000.0)
+    K = 3000
+
+    class S:
+        pass
+
+    def true_snr(res):
+        s = S()
+        s.dict, s.m, s.n, s.c = res.dict, res.m, res.n, res.c
+        r = x - cmp.synth(dicts, s, L)
+        return 10 * np.log10(float(x @ x) / float(r @ r))
+
+    no = cmp.mp_coef(dicts, x, 5e-2, K, 30.0)
+    yes = cmp.mp_coef_reset(dicts, x, 5e-2, K, 30.0, reset_db=-3.0)
+    assert yes.n_resets > 0
+    assert yes.stop == cmp.STOP_SNR
+    assert true_snr(yes) >= 29.5
+    assert true_snr(yes) > true_snr(no) + 1.0
