@@ -66,10 +66,13 @@ enum {
     MP_STOP_INVALID = 5    /* the signal holds NaN or Inf */
 };
 
-/* mp_plan_create flags */
+/* mp_plan_create flags (bit set) */
 enum {
     MP_ANALYSIS_FP32 = 0,   /* analysis as an FP32 DFT-GEMM on the SIMT cores (default) */
-    MP_ANALYSIS_BF16X3 = 1  /* analysis as a split-BF16 three-product DFT-GEMM on tcgen05 */
+    MP_ANALYSIS_BF16X3 = 1, /* analysis as a split-BF16 three-product DFT-GEMM on tcgen05;
+                               needs every a a multiple of 64 and every w/2 a multiple of a */
+    MP_PEDANTIC = 2         /* select by the real-pair energy drop of eq. projenfaster
+                               ("pedantic", Sec. 5) instead of |rho|^2 */
 };
 
 /*
@@ -80,7 +83,7 @@ enum {
  *               dividing the larger one (Sec. 2.1 compatibility)
  *   kern_thr    eps >= 0 of eq. truncgram, absolute: kernel entries with
  *               |h| <= eps are dropped (Fig. 1 uses 1e-4, i.e. -80 dB)
- *   flags       MP_ANALYSIS_*
+ *   flags       MP_ANALYSIS_* | MP_PEDANTIC
  *   cuda_stream cudaStream_t used by every call on this plan (NULL: legacy)
  * Computes on the device, in FP64, every cross-kernel h_{u,v} on the common
  * grid (a_min, M_max), thresholds it, splits it into dense FP32 tiles per

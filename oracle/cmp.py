@@ -18,6 +18,7 @@ _lib = None
 
 STOP_SNR, STOP_KMAX, STOP_NEGENERGY, STOP_ZEROMAX = 1, 2, 3, 4
 FLAG_FULLSCAN = 1
+FLAG_PEDANTIC = 2
 
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
@@ -141,12 +142,17 @@ def _run(fn, dicts, x, tail_args, kmax, extra_len, resets=None):
     return res
 
 
-def mp_coef(dicts, x, eps, kmax, snr_db, fullscan=False, planes=False):
-    """Coefficient-domain MP with G_eps (Alg. 1 + Alg. 3)."""
+def _flags(fullscan, pedantic):
+    return (FLAG_FULLSCAN if fullscan else 0) | (FLAG_PEDANTIC if pedantic else 0)
+
+
+def mp_coef(dicts, x, eps, kmax, snr_db, fullscan=False, planes=False, pedantic=False):
+    """Coefficient-domain MP with G_eps (Alg. 1 + Alg. 3); pedantic selects
+    by the pair energy drop of eq. projenfaster instead of |rho|^2."""
     L = len(x)
     P = sum((L // a) * (M // 2 + 1) for _, a, M in dicts)
     res = _run(lib().ora_mp_coef, dicts, x,
-               [float(eps), int(kmax), float(snr_db), FLAG_FULLSCAN if fullscan else 0],
+               [float(eps), int(kmax), float(snr_db), _flags(fullscan, pedantic)],
                kmax, 2 * P if planes else 0)
     if planes:
         e = res.extra.reshape(-1, 2)
@@ -160,19 +166,20 @@ def mp_coef(dicts, x, eps, kmax, snr_db, fullscan=False, planes=False):
     return res
 
 
-def mp_coef_reset(dicts, x, eps, kmax, snr_db, reset_it=0, reset_db=0.0, fullscan=False):
+def mp_coef_reset(dicts, x, eps, kmax, snr_db, reset_it=0, reset_db=0.0, fullscan=False,
+                  pedantic=False):
     """Alg. 2: coefficient-domain MP with resets (after reset_it selections
     since the last reset, or once the estimate fell reset_db (< 0) dB below
     the energy at the last reset)."""
     return _run(lib().ora_mp_coef_reset, dicts, x,
-                [float(eps), int(kmax), float(snr_db), FLAG_FULLSCAN if fullscan else 0,
+                [float(eps), int(kmax), float(snr_db), _flags(fullscan, pedantic),
                  int(reset_it), float(reset_db)], kmax, 0, resets=True)
 
 
-def mp_plain(dicts, x, kmax, snr_db, fullscan=False):
+def mp_plain(dicts, x, kmax, snr_db, fullscan=False, pedantic=False):
     """Plain signal-domain MP (exact re-analysis); extra = final residual."""
     return _run(lib().ora_mp_plain, dicts, x,
-                [int(kmax), float(snr_db), FLAG_FULLSCAN if fullscan else 0], kmax, len(x))
+                [int(kmax), float(snr_db), _flags(fullscan, pedantic)], kmax, len(x))
 
 
 def synth(dicts, res_or_atoms, L):

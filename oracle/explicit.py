@@ -54,7 +54,29 @@ def conj_partner_column(g, a, M, L, m, n):
     return D[:, ((M - m) % M) + n * M]
 
 
-def mp_definition(dicts, x, kmax):
+def pair_projection_energies(Dr, labels, dicts, r):
+    """Energy removed from r by projecting it onto the real span of each
+    reduced column and its conjugate (onto the real atom itself at m in
+    {0, M/2}), for every column: b^T G^-1 b with the 2 x 2 Gram matrix of
+    (Re d, Im d)."""
+    u1, u2 = Dr.real, Dr.imag
+    b1, b2 = u1.T @ r, u2.T @ r
+    g11 = np.sum(u1 * u1, axis=0)
+    g12 = np.sum(u1 * u2, axis=0)
+    g22 = np.sum(u2 * u2, axis=0)
+    out = np.empty(Dr.shape[1])
+    for p, (w, m, n) in enumerate(labels):
+        M = dicts[w][2]
+        if m == 0 or 2 * m == M:
+            out[p] = b1[p] ** 2 / g11[p]
+        else:
+            G = np.array([[g11[p], g12[p]], [g12[p], g22[p]]])
+            bb = np.array([b1[p], b2[p]])
+            out[p] = bb @ np.linalg.solve(G, bb)
+    return out
+
+
+def mp_definition(dicts, x, kmax, pedantic=False):
     """Matching pursuit with real atoms by definition.
 
     Selection: argmax |<r, d_p>| over the reduced multi-Gabor dictionary
@@ -62,7 +84,8 @@ def mp_definition(dicts, x, kmax):
     onto the real span of {d, conj d} (or onto d alone at m in {0, M/2}),
     computed with numpy least squares.  Returns the atoms (w, m, n, c) with c
     the complex coefficient of d in r_k - r_{k+1} = c d + conj(c) conj(d),
-    the energies ||r_k||^2, and the final residual."""
+    the energies ||r_k||^2, and the final residual.  pedantic: select the
+    column whose real-pair projection removes the most energy."""
     x = np.asarray(x, np.float64)
     L = x.size
     Dr, labels = multi_reduced(dicts, L)
@@ -70,7 +93,10 @@ def mp_definition(dicts, x, kmax):
     atoms, energies = [], [float(r @ r)]
     for _ in range(kmax):
         rho = Dr.conj().T @ r
-        p = int(np.argmax(np.abs(rho) ** 2))
+        if pedantic:
+            p = int(np.argmax(pair_projection_energies(Dr, labels, dicts, r)))
+        else:
+            p = int(np.argmax(np.abs(rho) ** 2))
         w, m, n = labels[p]
         g, a, M = dicts[w]
         d = Dr[:, p]

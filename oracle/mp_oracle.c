@@ -207,7 +207,27 @@ typedef struct {
     int* farg[64];          /* per frame: its (lowest) bin */
     double* fsecond[64];    /* per frame: second largest |rho|^2 */
     unsigned char* touched[64];
+    int pedantic;           /* selection score = energy drop of eq. projenfaster */
+    cplx* gam[64];          /* <d_m, conj d_m> used by the score, m = 0..M/2 */
 } mpstate;
+
+/* eq. projenfaster: energy removed by subtracting the real pair with the
+ * least-squares coefficient of eq. dualatprod (c^2 for m in {0, M/2}) */
+static double pair_energy(cplx rho, cplx gamma, int edge) {
+    if (edge) return creal(rho) * creal(rho);
+    double ag2 = creal(gamma) * creal(gamma) + cimag(gamma) * cimag(gamma);
+    cplx c = (rho - conj(gamma) * conj(rho)) / (1.0 - ag2);
+    double x = creal(c), y = cimag(c);
+    return 2.0 * (x * x + y * y + creal(gamma) * (x * x - y * y) - 2.0 * cimag(gamma) * x * y);
+}
+
+/* selection score of coefficient m of dictionary v: |rho|^2 (Sec. 5.1 as
+ * used in practice) or, pedantic, the pair energy drop (Sec. 5) */
+static double score(const mpstate* s, int v, int m, cplx r) {
+    if (!s->pedantic) return creal(r) * creal(r) + cimag(r) * cimag(r);
+    int edge = (m == 0) || (2 * m == s->M[v]);
+    return pair_energy(r, s->gam[v][m], edge);
+}
 
 static void frame_rescan(mpstate* s, int v, int64_t n) {
     int Mr = s->Mr[v];
@@ -215,7 +235,7 @@ static void frame_rescan(mpstate* s, int v, int64_t n) {
     double b = -1.0, b2 = -1.0;
     int arg = 0;
     for (int m = 0; m < Mr; ++m) {
-        double sc = creal(r[m]) * creal(r[m]) + cimag(r[m]) * cimag(r[m]);
+        double sc = score(s, v, m, r[m]);
         if (sc > b) { b2 = b; b = sc; arg = m; }
         else if (sc > b2) { b2 = sc; }
     }
@@ -243,6 +263,7 @@ static int state_init(mpstate* s, int W, const int* wl, const int* a, const int*
         s->fsecond[w] = (double*)malloc(sizeof(double) * (size_t)s->N[w]);
         s->farg[w] = (int*)malloc(sizeof(int) * (size_t)s->N[w]);
         s->touched[w] = (unsigned char*)calloc((size_t)s->N[w], 1);
+        s->gam[w] = (cplx*)calloc((size_t)s->Mr[w], sizeof(cplx));
     }
     return 0;
 }
@@ -250,7 +271,7 @@ static int state_init(mpstate* s, int W, const int* wl, const int* a, const int*
 static void state_free(mpstate* s) {
     for (int w = 0; w < s->W; ++w) {
         free(s->rho[w]); free(s->fbest[w]); free(s->fsecond[w]);
-        free(s->farg[w]); free(s->touched[w]);
+        free(s->farg[w]); free(s->touched[w]); free(s->gam[w]);
     }
 }
 
@@ -293,7 +314,7 @@ static double select_full(const mpstate* s, int* bu, int* bk, int64_t* bj) {
         for (int64_t n = 0; n < s->N[w]; ++n)
             for (int m = 0; m < s->Mr[w]; ++m) {
                 cplx r = s->rho[w][(size_t)n * s->Mr[w] + m];
-                double sc = creal(r) * creal(r) + cimag(r) * cimag(r);
+                double sc = score(s, w, m, r);
                 if (sc > best) { best = sc; *bu = w; *bk = m; *bj = n; }
             }
     return best;
@@ -310,6 +331,7 @@ static cplx dual_coef(cplx rho, cplx gamma, double* Edrop) {
 }
 
 #define ORA_FLAG_FULLSCAN 1
+#define ORA_FLAG_PEDANTIC 2
 
 typedef struct {
     int32_t* dict; int32_t* m; int64_t* n;
@@ -431,6 +453,16 @@ int ora_mp_coef_reset(int W, const int* wl, const int* a, const int* M, const do
                 }
             free(h);
         }
+    /* <d_m, conj d_m> from the truncated own kernel (Sec. 5.2) */
+    for (int u = 0; u < W; ++u) {
+        const kern* Kuu = &K[u * W + u];
+        int it0 = (0 - Kuu->tmin) / Kuu->an;
+        for (int m = 1; 2 * m < s.M[u]; ++m) {
+            cplx gv = Kuu->full[(size_t)it0 * Kuu->Mx + imod((int64_t)s.M[u] - 2 * m, s.M[u])];
+            s.gam[u][m] = cabs(gv) > eps ? gv : 0.0;
+        }
+    }
+    s.pedantic = (flags & ORA_FLAG_PEDANTIC) != 0;
 
     analyse_all(&s, x);
     double E0 = 0.0;
@@ -554,9 +586,20 @@ int ora_mp_plain(int W, const int* wl, const int* a, const int* M, const double*
     if (state_init(&s, W, wl, a, M, gcat, L)) return -1;
     double* r = (double*)malloc(sizeof(double) * (size_t)L);
     memcpy(r, x, sizeof(double) * (size_t)L);
-    analyse_all(&s, r);
     cplx* cs[64];
     for (int w = 0; w < W; ++w) cs[w] = cis_table(s.M[w]);
+    /* exact <d_m, conj d_m> = sum_t g(t)^2 e^{i 4 pi m t / M} */
+    for (int w = 0; w < W; ++w)
+        for (int m = 1; 2 * m < s.M[w]; ++m) {
+            cplx acc = 0.0;
+            for (int i = 0; i < s.w[w]; ++i) {
+                int t = i - s.w[w] / 2;
+                acc += s.g[w][i] * s.g[w][i] * cs[w][imod((int64_t)2 * m * t, s.M[w])];
+            }
+            s.gam[w][m] = acc;
+        }
+    s.pedantic = (flags & ORA_FLAG_PEDANTIC) != 0;
+    analyse_all(&s, r);
     double E0 = 0.0;
     for (int64_t l = 0; l < L; ++l) E0 += x[l] * x[l];
     double E = E0;

@@ -174,7 +174,7 @@ __global__ void k_tree_build(DevPlan P, const DevSig* __restrict__ sigs, int nsi
         int m = ch * CHUNK + lane;
         Entry e;
         e.val = row[m];
-        e.key = (m < D.Mr) ? make_key(e.val, fb + m) : 0ull;
+        e.key = (m < D.Mr) ? make_key_sel(e.val, fb + m, m, D, P.gam, P.pedantic) : 0ull;
         Entry r = warp_max_entry(e);
         if (lane == 0) l0[ch] = r;
         if (r.key > best.key) best = r;

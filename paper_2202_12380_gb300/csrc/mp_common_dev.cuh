@@ -14,9 +14,37 @@ __device__ __forceinline__ long long lmod(long long x, long long m) {
     return r < 0 ? r + m : r;
 }
 
-// selection key: |rho|^2 bits in the high word, inverted flat index low
+// selection key: score bits in the high word, inverted flat index low
 __device__ __forceinline__ unsigned long long make_key(float2 v, unsigned flat) {
     float s = fmaf(v.x, v.x, v.y * v.y);
+    return ((unsigned long long)__float_as_uint(s) << 32) |
+           (unsigned long long)(0xffffffffu - flat);
+}
+
+__device__ __forceinline__ float2 gamma_of(const DevDict& D, const float2* gam, int k) {
+    if (k < D.gam_lo) return gam[D.gam_off + k];
+    if (k >= D.Mr - D.gam_hi) return gam[D.gam_off + D.gam_lo + (k - (D.Mr - D.gam_hi))];
+    return make_float2(0.f, 0.f);
+}
+
+// pedantic selection score (Sec. 5): energy removed by the real pair with
+// the coefficient of eq. dualatprod, eq. projenfaster; c^2 at m in {0, M/2}.
+// Non-negative, so its float bits order like the values.
+__device__ __forceinline__ float pair_score(float2 v, int m, const DevDict& D, const float2* gam) {
+    if (m == 0 || 2 * m == D.M) return v.x * v.x;
+    const float2 g = gamma_of(D, gam, m);
+    if (g.x == 0.f && g.y == 0.f) return 2.f * fmaf(v.x, v.x, v.y * v.y);
+    const float inv = 1.f / (1.f - fmaf(g.x, g.x, g.y * g.y));
+    const float cx = (v.x - fmaf(g.x, v.x, g.y * v.y)) * inv;
+    const float cy = (v.y - fmaf(g.y, v.x, -g.x * v.y)) * inv;
+    const float c2 = fmaf(cx, cx, cy * cy), d2 = fmaf(cx, cx, -cy * cy);
+    return fmaxf(0.f, 2.f * (c2 + fmaf(g.x, d2, -2.f * g.y * cx * cy)));
+}
+
+__device__ __forceinline__ unsigned long long make_key_sel(float2 v, unsigned flat, int m,
+                                                           const DevDict& D, const float2* gam,
+                                                           int pedantic) {
+    const float s = pedantic ? pair_score(v, m, D, gam) : fmaf(v.x, v.x, v.y * v.y);
     return ((unsigned long long)__float_as_uint(s) << 32) |
            (unsigned long long)(0xffffffffu - flat);
 }

@@ -64,7 +64,7 @@ struct DevPlan {
     int ncls;  // class descriptors
     int ngam;  // entries of the compact <d, conj d> pool
     int ncis;  // entries of the modulation tables
-    int pad;
+    int pedantic;  // selection by the pair energy drop (MP_PEDANTIC)
     DevDict d[MAXW];
     DevPair p[MAXW * MAXW];
     const DevClass* cls;

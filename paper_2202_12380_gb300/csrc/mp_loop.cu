@@ -134,11 +134,6 @@ __device__ __forceinline__ int term_q(const Term& T, int n, int Nv, int av, int 
     return (int)(((unsigned long long)T.kk * tm) % (unsigned)Mu);
 }
 
-__device__ __forceinline__ float2 gamma_of(const DevDict& D, const float2* sgam, int k) {
-    if (k < D.gam_lo) return sgam[D.gam_off + k];
-    if (k >= D.Mr - D.gam_hi) return sgam[D.gam_off + D.gam_lo + (k - (D.Mr - D.gam_hi))];
-    return make_float2(0.f, 0.f);
-}
 
 __device__ __forceinline__ unsigned mapa_u32(unsigned addr, int rank) {
     unsigned r;
@@ -609,7 +604,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                         if (hit0[q] || hit1[q]) prow[m] = x2;
                         Entry e;
                         e.val = x2;
-                        e.key = (m < Dv.Mr) ? make_key(x2, S.fbase[v] + ((unsigned)n << Dv.msh) + m)
+                        e.key = (m < Dv.Mr) ? make_key_sel(x2, S.fbase[v] + ((unsigned)n << Dv.msh) + m,
+                                                            m, Dv, sgam, P.pedantic)
                                             : 0ull;
                         const Entry rr = warp_max_entry(e);
                         if (lane == 0) S.l0[v][(long long)n * Dv.nch + chunk[q]] = rr;

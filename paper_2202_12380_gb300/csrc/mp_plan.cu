@@ -242,7 +242,7 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
         mpg_set_error("mp_plan_create: kernel threshold must be finite and >= 0");
         return MP_EINVAL;
     }
-    if (flags > MP_ANALYSIS_BF16X3) {
+    if (flags & ~(unsigned)(MP_ANALYSIS_BF16X3 | MP_PEDANTIC)) {
         mpg_set_error("mp_plan_create: unknown flags %u", flags);
         return MP_EINVAL;
     }
@@ -543,6 +543,7 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
         p->dp.gam = p->d_gam;
         p->dp.g32 = p->d_g32;
         p->dp.cis = p->d_cis32;
+        p->dp.pedantic = (flags & MP_PEDANTIC) ? 1 : 0;
     }
     for (int w = 0; w < W; ++w) {
         cudaFree(d_win[w]);

@@ -20,7 +20,7 @@ from . import build as _build
 MP_OK, MP_EINVAL, MP_ENOTCOMPAT, MP_ENOMEM, MP_ECUDA, MP_ETIMEOUT = 0, -1, -2, -3, -4, -5
 MP_STOP_NONE, MP_STOP_SNR, MP_STOP_KMAX, MP_STOP_NEGENERGY, MP_STOP_ZEROMAX, MP_STOP_INVALID = \
     0, 1, 2, 3, 4, 5
-MP_ANALYSIS_FP32, MP_ANALYSIS_BF16X3 = 0, 1
+MP_ANALYSIS_FP32, MP_ANALYSIS_BF16X3, MP_PEDANTIC = 0, 1, 2
 
 ATOM_DTYPE = np.dtype([("dict", "<i4"), ("m", "<i4"), ("n", "<i8"), ("re", "<f4"), ("im", "<f4")])
 

@@ -421,3 +421,24 @@ def test_resets_batched_only_flagged_signals_reanalysed():
         ref = cmp.mp_coef_reset(dicts, x.astype(np.float64), eps, K, 200.0, reset_db=-2.0)
         atoms, errs = mg.mp_get_atoms(st, b), mg.mp_get_errors(st, b)
         compare(atoms, errs, float(np.sum(x.astype(np.float64) ** 2)), ref, min_checked=20)
+
+
+# ------------------------------------------------ pedantic selection -------
+
+@pytest.mark.parametrize("kind", ["single", "multi3", "mixed"])
+def test_pedantic_parity(kind):
+    """MP_PEDANTIC: selection by the real-pair energy drop (eq. projenfaster)
+    on the GPU against the oracle's pedantic pursuit."""
+    L, dicts = _workload_small(kind)
+    x = inputs.as_f32(inputs.mixture(L, 37, fs=16000.0) + 0.3)
+    K = 300
+    ref = cmp.mp_coef(dicts, x.astype(np.float64), 1e-4, K, 200.0, pedantic=True)
+    plan = _plan(dicts, 1e-4, mg.MP_PEDANTIC)
+    st = mg.mp_analyze(plan, [torch.from_numpy(x).cuda()])
+    n, stop, q = mg.mp_run(st, K, 200.0)
+    atoms, errs = mg.mp_get_atoms(st, 0), mg.mp_get_errors(st, 0)
+    r = compare(atoms, errs, float(np.sum(x.astype(np.float64) ** 2)), ref, min_checked=60)
+    # pedantic and non-pedantic pursuits differ on this offset signal
+    plain_sel = cmp.mp_coef(dicts, x.astype(np.float64), 1e-4, K, 200.0)
+    assert not np.array_equal(plain_sel.m, ref.m) or not np.array_equal(plain_sel.n, ref.n)
+    print(kind, r)

@@ -230,3 +230,46 @@ def test_resets_restore_convergence_with_coarse_threshold():
     assert yes.stop == cmp.STOP_SNR
     assert true_snr(yes) >= 29.5
     assert true_snr(yes) > true_snr(no) + 1.0
+
+
+# ---------------------------------------------------------- pedantic ------
+
+def test_pedantic_plain_matches_definition():
+    """Pedantic selection (Sec. 5: the score is the pair energy drop of eq.
+    projenfaster) equals choosing, by brute force on explicit matrices, the
+    real atom whose projection removes the most energy."""
+    L = 96
+    dicts = _tiny_dicts()
+    x = np.random.default_rng(8).standard_normal(L)
+    K = 30
+    atoms, energies, _ = explicit.mp_definition(dicts, x, K, pedantic=True)
+    res = cmp.mp_plain(dicts, x, K, 400.0, pedantic=True, fullscan=True)
+    for i, (w, m, n, c) in enumerate(atoms):
+        assert (res.dict[i], res.m[i], res.n[i]) == (w, m, n), i
+        assert abs(res.c[i] - c) < 1e-10 * max(1.0, abs(c))
+    assert np.max(np.abs(res.E - energies[1:])) < 1e-10 * energies[0]
+
+
+def test_pedantic_differs_and_decays_faster():
+    """The pedantic score weighs real pairs by 2 against edge atoms, so the
+    sequences differ, and each pedantic step removes at least as much true
+    energy as the non-pedantic one from the same residual (first step)."""
+    L = 1024
+    dicts = [(inputs.blackman(w), w // 4, w) for w in (32, 128)]
+    x = inputs.mixture(L, 18, fs=8000.0) + 0.5
+    a = cmp.mp_plain(dicts, x, 60, 400.0)
+    b = cmp.mp_plain(dicts, x, 60, 400.0, pedantic=True)
+    assert not (np.array_equal(a.dict, b.dict) and np.array_equal(a.m, b.m)
+                and np.array_equal(a.n, b.n))
+    assert b.E[0] <= a.E[0] + 1e-12 * a.E0
+
+
+def test_pedantic_coef_eps0_equals_plain():
+    L = 2048
+    dicts = [(inputs.blackman(w), w // 4, w) for w in (32, 64, 128)]
+    x = inputs.mixture(L, 19, fs=8000.0)
+    a = cmp.mp_plain(dicts, x, 120, 400.0, pedantic=True, fullscan=True)
+    b = cmp.mp_coef(dicts, x, 0.0, 120, 400.0, pedantic=True, fullscan=True)
+    assert np.array_equal(a.dict, b.dict) and np.array_equal(a.m, b.m)
+    assert np.array_equal(a.n, b.n)
+    assert np.max(np.abs(a.c - b.c) / np.abs(a.c)) < 1e-9
