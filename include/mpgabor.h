@@ -127,7 +127,9 @@ int mp_plan_gamma(const mp_plan* plan, int u, float* gamma_host, int64_t cap_flo
  *            stream work)
  * If *state is NULL a new state is allocated; if it is non-NULL it must come
  * from the same plan with the same B and lengths and is reused (all previous
- * atoms are discarded).  Asynchronous on the plan's stream.
+ * atoms are discarded).  Asynchronous on the plan's stream; reusing a state,
+ * mp_analyze (device pointers) followed by mp_run_async can be captured into
+ * a CUDA graph (the tensor-core error check is skipped while capturing).
  * mp_analyze_host is the same with host pointers; it copies each signal to
  * the device inside the call (end-to-end path).
  */
@@ -164,6 +166,17 @@ int mp_run_async(mp_state* state, int64_t K_max, double target_snr_db);
 int mp_get_status(mp_state* state, int64_t* n_atoms, int* stop_reason, double* final_snr_db);
 /* seconds of device time after which a launch returns MP_ETIMEOUT (<= 0: none) */
 int mp_state_set_time_limit(mp_state* state, double seconds);
+
+/*
+ * Launch shape of the MP loop (tuning): threads per CTA (128, 256, 512 or
+ * 1024) and CTAs per signal (thread-block cluster of 1, 2, 4, 8 or 16; more
+ * than one needs every N_w = L/a_w divisible by it).  The default is chosen
+ * from the number of signals; threads = cluster = 0 restores it.  Returns
+ * MP_EINVAL for a shape this state cannot run.  mp_state_get_launch reports
+ * the current shape.  Results do not depend on the shape.
+ */
+int mp_state_set_launch(mp_state* state, int threads, int cluster);
+int mp_state_get_launch(const mp_state* state, int* threads, int* cluster);
 
 /*
  * Resets, Alg. 2 (the paper's reset options, Sec. 7): mp_run interrupts the

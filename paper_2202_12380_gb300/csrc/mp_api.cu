@@ -407,7 +407,9 @@ int analysis_pass(mp_state* s, int flagged) {
                               flagged));
     }
     CKR(launch_group_build(s->d_sigs, B, s->d_group_prefix, s->total_groups, p->W, st, flagged));
-    if (tc) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CKR(cudaStreamIsCapturing(st, &cap));
+    if (tc && cap == cudaStreamCaptureStatusNone) {
         // the tensor-core kernel bounds its waits; report an expired wait
         int err = 0;
         CKR(cudaMemcpyAsync(&err, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -586,6 +588,38 @@ extern "C" int mp_run(mp_state* s, int64_t K_max, double target_snr_db, int64_t*
         if (rc) return rc;
     }
     return mp_get_status(s, n_atoms, stop_reason, final_snr_db);
+}
+
+extern "C" int mp_state_set_launch(mp_state* s, int threads, int cluster) {
+    if (!s) {
+        mpg_set_error("mp_state_set_launch: null state");
+        return MP_EINVAL;
+    }
+    if (threads == 0 && cluster == 0) {
+        mp_loop_shape(s->plan->dp, s->hs.data(), s->B, s->plan->num_sms, &s->threads, &s->cs,
+                      &s->smem);
+        return MP_OK;
+    }
+    size_t smem = 0;
+    if (!mp_loop_shape_ok(s->plan->dp, s->hs.data(), s->B, threads, cluster, &smem)) {
+        mpg_set_error("mp_state_set_launch: %d threads x cluster %d is not feasible for this "
+                      "state", threads, cluster);
+        return MP_EINVAL;
+    }
+    s->threads = threads;
+    s->cs = cluster;
+    s->smem = smem;
+    return MP_OK;
+}
+
+extern "C" int mp_state_get_launch(const mp_state* s, int* threads, int* cluster) {
+    if (!s) {
+        mpg_set_error("mp_state_get_launch: null state");
+        return MP_EINVAL;
+    }
+    if (threads) *threads = s->threads;
+    if (cluster) *cluster = s->cs;
+    return MP_OK;
 }
 
 extern "C" int mp_state_set_resets(mp_state* s, int64_t reset_every, double reset_err_db) {

@@ -132,6 +132,7 @@ cudaError_t launch_mp_loop(const DevPlan& P, DevSig* d_sigs, const int* d_order,
                            double reset_scale = 0.0);
 void mp_loop_shape(const DevPlan& P, const DevSig* hs, int B, int num_sms, int* threads, int* cs,
                    size_t* smem);
+bool mp_loop_shape_ok(const DevPlan& P, const DevSig* hs, int B, int threads, int c, size_t* smem);
 cudaError_t launch_synth(const DevPlan& P, const DevSig* d_sig, long long natoms, float* y,
                          long long L, cudaStream_t st);
 cudaError_t launch_resid_energy(const DevSig* d_sig, const float* y, long long L,

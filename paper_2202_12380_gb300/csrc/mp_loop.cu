@@ -768,6 +768,30 @@ int mp_loop_threads(int nsig, int num_sms) {
     return nsig <= num_sms ? 512 : 256;
 }
 
+// feasibility of a requested launch shape (threads per CTA, cluster size)
+bool mp_loop_shape_ok(const DevPlan& P, const DevSig* hs, int B, int threads, int c, size_t* smem) {
+    if (threads != 128 && threads != 256 && threads != 512 && threads != 1024) return false;
+    if (c != 1 && c != 2 && c != 4 && c != 8 && c != 16) return false;
+    if (c == 1) {
+        int tmax = 1;
+        for (int b = 0; b < B; ++b) tmax = hs[b].T > tmax ? hs[b].T : tmax;
+        *smem = mp_loop_smem_bytes(P, tmax, threads, 1);
+        return *smem <= 227 * 1024;
+    }
+    int lt = 0;
+    for (int b = 0; b < B; ++b) {
+        int t = 0;
+        for (int w = 0; w < P.W; ++w) {
+            if (hs[b].N[w] % c) return false;
+            t += (int)(hs[b].N[w] / c);
+        }
+        lt = t > lt ? t : lt;
+    }
+    if (lt > TOPCAP) return false;
+    *smem = mp_loop_smem_bytes(P, lt, threads, c);
+    return mp_loop_max_clusters(threads, c, *smem) >= 1;
+}
+
 // launch shape for B signals: threads per CTA, cluster size and dynamic
 // shared memory.  Clusters give a signal several SMs while there are SMs to
 // spare; they need every N_w divisible by the cluster size and the per-CTA

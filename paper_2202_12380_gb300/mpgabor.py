@@ -29,7 +29,7 @@ EXPORTS = [
     "mp_plan_tile_info", "mp_plan_tile", "mp_plan_gamma", "mp_analyze", "mp_analyze_host",
     "mp_state_coefficients", "mp_run", "mp_run_async", "mp_get_status", "mp_state_set_time_limit",
     "mp_get_atoms", "mp_get_errors", "mp_synthesize", "mp_state_destroy", "mp_last_error",
-    "mp_decompose_static", "mp_state_set_resets",
+    "mp_decompose_static", "mp_state_set_resets", "mp_state_set_launch", "mp_state_get_launch",
 ]
 
 _lib = None
@@ -78,6 +78,8 @@ def lib():
         "mp_last_error": ([], C.c_char_p),
         "mp_decompose_static": ([vp, vp, i64, i64, dbl, vp, vp, P(i64), P(i32), P(dbl)], i32),
         "mp_state_set_resets": ([vp, i64, dbl], i32),
+        "mp_state_set_launch": ([vp, i32, i32], i32),
+        "mp_state_get_launch": ([vp, P(i32), P(i32)], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -277,6 +279,18 @@ def mp_get_status(state: State):
 
 def mp_state_set_time_limit(state: State, seconds: float):
     _check(lib().mp_state_set_time_limit(state.handle, float(seconds)))
+
+
+def mp_state_set_launch(state: State, threads: int = 0, cluster: int = 0):
+    """Pin the MP launch shape (threads per CTA, CTAs per signal); 0, 0
+    restores the default."""
+    _check(lib().mp_state_set_launch(state.handle, int(threads), int(cluster)))
+
+
+def mp_state_get_launch(state: State):
+    t, c = C.c_int(), C.c_int()
+    _check(lib().mp_state_get_launch(state.handle, C.byref(t), C.byref(c)))
+    return t.value, c.value
 
 
 def mp_state_set_resets(state: State, reset_every: int = 0, reset_err_db: float = 0.0):

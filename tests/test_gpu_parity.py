@@ -442,3 +442,37 @@ def test_pedantic_parity(kind):
     plain_sel = cmp.mp_coef(dicts, x.astype(np.float64), 1e-4, K, 200.0)
     assert not np.array_equal(plain_sel.m, ref.m) or not np.array_equal(plain_sel.n, ref.n)
     print(kind, r)
+
+
+# ------------------------------------------ graphs, launch shapes, tuning --
+
+def test_graph_replay_and_autotune():
+    """analysis + MP captured in a CUDA graph and replayed gives the same
+    atoms as direct calls; the autotuner returns a feasible launch shape and
+    the pinned shape does not change the result."""
+    from paper_2202_12380_gb300 import autotune
+    dicts = [(inputs.blackman(w), w // 4, w) for w in (128, 256, 512)]
+    xs = [inputs.as_f32(inputs.mixture(L, 60 + i, fs=16000.0)) for i, L in enumerate((8192, 16384, 4096))]
+    stream = torch.cuda.Stream()
+    plan = mg.mp_plan_create([d[0] for d in dicts], [d[1] for d in dicts], [d[2] for d in dicts],
+                             1e-4, 0, stream)
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    shape, ms = autotune.tune(plan, xd, k_probe=100, stream=stream, repeats=1)
+    assert shape in ms and len(ms) >= 2
+    st = mg.mp_analyze(plan, xd)
+    mg.mp_run(st, 250, 200.0)
+    direct = [mg.mp_get_atoms(st, b) for b in range(3)]
+    mg.mp_state_set_launch(st, *shape)
+    assert mg.mp_state_get_launch(st) == tuple(shape)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+        mg.mp_analyze(plan, xd, st)
+        mg.mp_run_async(st, 250, 200.0)
+    for _ in range(2):
+        with torch.cuda.stream(stream):
+            g.replay()
+        stream.synchronize()
+        for b in range(3):
+            assert np.array_equal(mg.mp_get_atoms(st, b), direct[b])
+    with pytest.raises(mg.MPError):
+        mg.mp_state_set_launch(st, 96, 1)
