@@ -1,13 +1,14 @@
 // Persistent matching-pursuit loop (Alg. 1 with the residual update of
-// Alg. 3): one CTA per signal, iterating selection -> real-pair adjustment
-// -> energy bookkeeping -> coefficient-domain update of every dictionary ->
-// max-tree repair, entirely on the device.
+// Alg. 3): one CTA (or one thread-block cluster) per signal, iterating
+// selection -> real-pair adjustment -> energy bookkeeping -> coefficient-
+// domain update of every dictionary -> max-tree repair, entirely on the
+// device.
 //
 // Max tree (Sec. 5.1).  Level 0 (per frame and 32-bin chunk) and level 1
 // (per frame) live in global memory next to the coefficient planes; the top
 // level (one Entry per frame, or per group of 2^gshift frames) lives in
-// shared memory and is scanned by the whole CTA every iteration (a few
-// shared loads per thread), so there is no further level to maintain.
+// shared memory and is scanned by the whole CTA every iteration, so there is
+// no further level to maintain.
 //
 // One iteration:
 //   1. every thread scans its share of the top level; warp bests are reduced
@@ -15,18 +16,23 @@
 //   2. with a cluster, each CTA sends its best to every CTA of the cluster
 //      (st.async into distributed shared memory, completing bytes on the
 //      receiver's mbarrier) and waits, bounded, for all of them; every warp
-//      then takes the same selection, adjusts the coefficient to the
-//      real-pair coefficient (eqs. dualatprod / projenfaster) and one thread
+//      then takes the same selection and adjusts the coefficient to the
+//      real-pair coefficient (eqs. dualatprod / projenfaster); one thread
 //      keeps E in FP64 and writes the atom list;
-//   3. warps are assigned to dictionaries (warp w serves w mod W); a warp
-//      builds its dictionary's update -- the atom's and the conjugate
-//      partner's class tile, the column hull and the touched 32-bin chunks
-//      as a bit mask -- and runs one job per owned touched frame: load the
-//      frame's level-0 entries together with the touched chunks of the plane
-//      and the matching tile entries, subtract both terms (eq.
-//      fastkernupdate with the modulation of eq. hkj, looked up in an FP64-
-//      rounded table), recompute the touched chunks' level-0 entries, the
-//      frame's level-1 entry and its top-level slot; barrier.
+//   3. warp v builds dictionary v's update for this iteration -- the class
+//      tiles of the atom and of its conjugate partner, their first row and
+//      column, the modulation index of column 0 and its step, the frames of
+//      the column hull owned by this CTA, and the list of touched 32-bin
+//      chunks -- into shared memory; barrier;
+//   4. the frame jobs of all dictionaries are dealt to the warps from one
+//      flat index.  A job loads the frame's level-0 entries together with
+//      the touched chunks of the plane and the matching tile entries,
+//      subtracts both terms (eq. fastkernupdate with the modulation of eq.
+//      hkj, looked up in an FP64-rounded table), recomputes the touched
+//      chunks' level-0 entries, the frame's level-1 entry and its top-level
+//      slot; barrier;
+//   5. (single CTA with grouped top level) the groups of touched frames are
+//      rebuilt, one thread per group; barrier.
 //
 // Clusters.  A signal may be given a thread-block cluster of CS CTAs (on CS
 // SMs) instead of one CTA: frame n of every dictionary belongs to CTA
@@ -44,20 +50,26 @@
 namespace mpg {
 namespace {
 
-constexpr int MAXL0 = 4;   // level-0 entries held per lane (larger frames loop)
-constexpr int CB = 4;      // touched chunks processed per batch of loads
+constexpr int MAXL0 = 4;   // level-0 entries held per lane (larger frames reload)
+constexpr int CB = 4;      // touched chunks per batch of loads
 
-// one term (the atom or its conjugate partner) of the update of dictionary v
-struct Term {
-    int active;
-    int Arow;   // first tile row, as a bin of dictionary v, in [0, M_v)
-    int R;
-    int Acol;   // first tile column, as a frame of dictionary v, in [0, N_v)
-    int C;
-    int kk;     // frequency index (in dictionary u) of this atom
-    int tau0;   // tau of tile column 0
-    int a0;     // unwrapped first column (for the column hull)
-    long long tile;  // float2 offset of the class tile
+// One dictionary's part of an iteration's update.  Term 0 is the selected
+// atom, term 1 its conjugate partner (M_u - k, j).  A term's tile covers
+// rows Arow .. Arow + R - 1 (mod M_v) and frames Acol .. Acol + C - 1
+// (mod N_v); column c carries the modulation e^{i 2 pi q / M_u},
+// q = qb + c dq (mod M_u).
+struct __align__(16) VJob {
+    int act0, act1;
+    int Arow0, Arow1;
+    int R0, R1;
+    int Acol0, Acol1;
+    int C0, C1;
+    int qb0, qb1;
+    int dq0, dq1;
+    int nstart, cnt;  // owned hull frames nstart + f CS (mod N_v), f < cnt
+    long long tile0, tile1;  // float2 offsets of the class tiles
+    int nlist;               // touched chunks, listed in the chunk list of v
+    int pad[3];
 };
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -70,70 +82,11 @@ __device__ __forceinline__ unsigned long long gtimer() {
     return t;
 }
 
-__device__ __forceinline__ int imod(int x, int m) {
-    int r = x % m;
-    return r < 0 ? r + m : r;
+// x mod M for x in [-M, 2M)
+__device__ __forceinline__ int wrap2(int x, int M) {
+    x += x < 0 ? M : 0;
+    return x >= M ? x - M : x;
 }
-
-// term t of dictionary v for the selected (u, k, j)
-__device__ __forceinline__ Term make_term(const DevDict* sd, const DevPair* sp,
-                                          const DevClass* scls, int W, const DevSig& S, int u,
-                                          int k, int j, bool edge, int v, int t) {
-    Term T;
-    T.active = 0;
-    T.Arow = T.R = T.Acol = T.C = T.kk = T.tau0 = T.a0 = 0;
-    T.tile = 0;
-    if (t == 1 && edge) return T;
-    const DevDict& Du = sd[u];
-    const DevDict& Dv = sd[v];
-    const DevPair& PR = sp[u * W + v];
-    const int Mu = Du.M, Mv = Dv.M, au = Du.a, av = Dv.a;
-    const int kk = t == 0 ? k : Mu - k;
-    const int ct = PR.rt_sh >= 0 ? (j & (PR.rt - 1)) : j % PR.rt;
-    const int cf = PR.rf_sh >= 0 ? (kk & (PR.rf - 1)) : kk % PR.rf;
-    const DevClass& C = scls[PR.cls_base + cf * PR.rt + ct];
-    if (C.R == 0) return T;
-    const int base_m = PR.mratio ? kk * PR.mratio
-                                 : (PR.rf_sh >= 0 ? (kk - cf) >> PR.rf_sh : (kk - cf) / PR.rf);
-    const int base_n = PR.aratio ? j * PR.aratio
-                                 : (PR.rt_sh >= 0 ? (j - ct) >> PR.rt_sh : (j - ct) / PR.rt);
-    T.Arow = Dv.Mmask ? ((base_m + C.i_lo) & Dv.Mmask) : imod(base_m + C.i_lo, Mv);
-    T.R = C.R;
-    // any stored row (0 .. M_v/2) inside [Arow, Arow + R) mod M_v ?
-    const bool rows = (T.Arow < Dv.Mr) || (T.Arow + T.R > Mv);
-    if (!rows) return T;
-    T.active = 1;
-    T.C = C.C;
-    T.kk = kk;
-    T.tau0 = C.c_lo * av - ct * au;
-    T.a0 = base_n + C.c_lo;
-    T.Acol = S.Nmask[v] ? (T.a0 & S.Nmask[v]) : imod(T.a0, (int)S.N[v]);
-    T.tile = C.off;
-    return T;
-}
-
-__device__ __forceinline__ bool term_hit(const Term& T, int m, int n, int Mv, int Nv, int* off) {
-    if (!T.active) return false;
-    int cc = n - T.Acol;
-    if (cc < 0) cc += Nv;
-    if (cc >= T.C) return false;
-    int i = m - T.Arow;
-    if (i < 0) i += Mv;
-    if (i >= T.R) return false;
-    *off = cc * T.R + i;
-    return true;
-}
-
-// index q = (k tau) mod M_u of the column's modulation e^{i 2 pi k tau / M_u}
-__device__ __forceinline__ int term_q(const Term& T, int n, int Nv, int av, int Mu, int Mumask) {
-    int cc = n - T.Acol;
-    if (cc < 0) cc += Nv;
-    const int tau = T.tau0 + cc * av;
-    if (Mumask) return (int)(((unsigned)T.kk * ((unsigned)tau & (unsigned)Mumask)) & (unsigned)Mumask);
-    const unsigned tm = (unsigned)imod(tau, Mu);
-    return (int)(((unsigned long long)T.kk * tm) % (unsigned)Mu);
-}
-
 
 __device__ __forceinline__ unsigned mapa_u32(unsigned addr, int rank) {
     unsigned r;
@@ -164,113 +117,135 @@ __device__ __forceinline__ bool xbar_try(unsigned addr, unsigned parity) {
     return ok != 0;
 }
 
-// one dictionary's part of the update, shared by the warps that serve it;
-// all fields are scalars so the struct lives in registers
-struct DictJob {
-    Term t0, t1;
-    int nstart;  // first frame of the hull owned by this CTA
-    int cnt;     // owned frames of the hull
-    // chunk ranges [l, h): a0, a1 of the atom (na of them), b0, b1 of the
-    // partner (nb of them)
-    int a0l, a0h, a1l, a1h, b0l, b0h, b1l, b1h;
-    int na, nb;
-    // the same set as a bit mask over chunks cbase .. cbase + 63 (cwide: the
-    // set spans more than 64 chunks and is walked range by range instead)
-    int cbase, cend;
-    unsigned long long cmask;
-    bool cwide;
-};
-
-// chunk ranges of a term's stored rows: up to two, as scalars
-__device__ __forceinline__ int term_chunks2(const Term& t, int Mv, int Mr, int& l0, int& h0, int& l1,
-                                            int& h1) {
-    l0 = h0 = l1 = h1 = 0;
-    if (!t.active) return 0;
-    int n = 0;
-    const int e1 = min(min(t.Arow + t.R, Mv), Mr);
-    if (e1 > t.Arow) {
-        l0 = t.Arow / CHUNK;
-        h0 = (e1 - 1) / CHUNK + 1;
-        n = 1;
-    }
-    if (t.Arow + t.R > Mv) {
-        const int b1 = min(t.Arow + t.R - Mv, Mr);
-        if (b1 > 0) {
-            const int l = 0, h = (b1 - 1) / CHUNK + 1;
-            if (n == 0) { l0 = l; h0 = h; } else { l1 = l; h1 = h; }
-            ++n;
-        }
-    }
-    return n;
-}
-
-__device__ __forceinline__ bool in_ranges(const DictJob& J, int c) {
-    bool t = false;
-    t |= (J.na > 0) & (c >= J.a0l) & (c < J.a0h);
-    t |= (J.na > 1) & (c >= J.a1l) & (c < J.a1h);
-    t |= (J.nb > 0) & (c >= J.b0l) & (c < J.b0h);
-    t |= (J.nb > 1) & (c >= J.b1l) & (c < J.b1h);
-    return t;
-}
-
-
-__device__ __forceinline__ void dict_job(const DevDict* sd, const DevPair* sp, const DevClass* scls,
-                                         int W, const DevSig& S, int u, int kk, int j, bool edge,
-                                         int v, int rank, int CS, DictJob& J) {
-    J.t0 = make_term(sd, sp, scls, W, S, u, kk, j, edge, v, 0);
-    J.t1 = make_term(sd, sp, scls, W, S, u, kk, j, edge, v, 1);
+// Dictionary v's update for the selected atom (u, k, j), built by one warp
+// (every lane computes the scalars; the lanes split the chunk list).
+__device__ __forceinline__ void build_vjob(const DevDict* sd, const DevPair* sp,
+                                           const DevClass* scls, int W, const DevSig& S, int u,
+                                           int kk, int j, bool edge, int v, int rank, int CS,
+                                           int cs_sh, int lane, VJob* out,
+                                           unsigned short* clist) {
+    const DevDict& Du = sd[u];
     const DevDict& Dv = sd[v];
+    const DevPair& PR = sp[u * W + v];
+    const int Mu = Du.M, Mumask = Du.Mmask, au = Du.a;
+    const int Mv = Dv.M, Mr = Dv.Mr, av = Dv.a;
     const int Nv = (int)S.N[v];
-    J.cnt = 0;
-    J.nstart = 0;
-    int lo = 0, hi = 0;
-    bool any = false;
-    if (J.t0.active) { lo = J.t0.a0; hi = J.t0.a0 + J.t0.C; any = true; }
-    if (J.t1.active) {
-        if (any) { lo = min(lo, J.t1.a0); hi = max(hi, J.t1.a0 + J.t1.C); }
-        else { lo = J.t1.a0; hi = J.t1.a0 + J.t1.C; any = true; }
+    const int ct = PR.rt_sh >= 0 ? (j & (PR.rt - 1)) : j % PR.rt;
+    const int base_n = PR.aratio ? j * PR.aratio
+                                 : (PR.rt_sh >= 0 ? j >> PR.rt_sh : (j - ct) / PR.rt);
+    int act[2], Arow[2], R[2], Acol[2], Cc[2], a0[2], qb[2], dq[2];
+    long long tile[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int kt = t ? Mu - kk : kk;
+        const int cf = PR.rf_sh >= 0 ? (kt & (PR.rf - 1)) : kt % PR.rf;
+        const DevClass C = scls[PR.cls_base + cf * PR.rt + ct];
+        const int base_m = PR.mratio ? kt * PR.mratio
+                                     : (PR.rf_sh >= 0 ? kt >> PR.rf_sh : (kt - cf) / PR.rf);
+        Arow[t] = wrap2(base_m + C.i_lo, Mv);
+        R[t] = C.R;
+        // any stored row (0 .. M_v/2) inside [Arow, Arow + R) mod M_v ?
+        act[t] = (t == 0 || !edge) && C.R > 0 && (Arow[t] < Mr || Arow[t] + C.R > Mv);
+        a0[t] = base_n + C.c_lo;
+        Acol[t] = wrap2(a0[t], Nv);
+        Cc[t] = C.C;
+        const int tau0 = C.c_lo * av - ct * au;
+        if (Mumask) {
+            qb[t] = (int)(((unsigned)kt * (unsigned)tau0) & (unsigned)Mumask);
+            dq[t] = (int)(((unsigned)kt * (unsigned)av) & (unsigned)Mumask);
+        } else {
+            qb[t] = (int)lmod((long long)kt * tau0, Mu);
+            dq[t] = (int)(((long long)kt * av) % Mu);
+        }
+        tile[t] = C.off;
     }
-    if (any) {
-        int ns, nf;
+    // frames of the column hull of both terms owned by this CTA
+    int cnt = 0, nstart = 0;
+    if (act[0] | act[1]) {
+        const int lo = act[0] && act[1] ? min(a0[0], a0[1]) : (act[0] ? a0[0] : a0[1]);
+        const int hi = act[0] && act[1] ? max(a0[0] + Cc[0], a0[1] + Cc[1])
+                                        : (act[0] ? a0[0] + Cc[0] : a0[1] + Cc[1]);
         const int nc = hi - lo;
-        if (nc >= Nv) { ns = 0; nf = Nv; }
-        else { ns = S.Nmask[v] ? (lo & S.Nmask[v]) : imod(lo, Nv); nf = nc; }
-        const int i0 = imod(rank - ns, CS);
-        J.nstart = ns + i0;
-        J.cnt = nf > i0 ? (nf - i0 + CS - 1) / CS : 0;
+        const int ns = nc >= Nv ? 0 : wrap2(lo, Nv);
+        const int nf = nc >= Nv ? Nv : nc;
+        const int i0 = (rank - ns) & (CS - 1);
+        nstart = ns + i0;
+        cnt = nf > i0 ? ((nf - i0 + CS - 1) >> cs_sh) : 0;
     }
-    J.na = term_chunks2(J.t0, Dv.M, Dv.Mr, J.a0l, J.a0h, J.a1l, J.a1h);
-    J.nb = term_chunks2(J.t1, Dv.M, Dv.Mr, J.b0l, J.b0h, J.b1l, J.b1h);
-    int clo = 1 << 30, chi = 0;
-    if (J.na > 0) { clo = min(clo, J.a0l); chi = max(chi, J.a0h); }
-    if (J.na > 1) { clo = min(clo, J.a1l); chi = max(chi, J.a1h); }
-    if (J.nb > 0) { clo = min(clo, J.b0l); chi = max(chi, J.b0h); }
-    if (J.nb > 1) { clo = min(clo, J.b1l); chi = max(chi, J.b1h); }
-    if (chi <= clo) { clo = 0; chi = 0; }
-    J.cbase = clo;
-    J.cend = chi;
-    J.cwide = chi - clo > 64;
-    unsigned long long m = 0;
-    if (!J.cwide) {
-        auto add = [&](int l, int h) {
-            const int n = h - l;
-            const unsigned long long bits = n >= 64 ? ~0ull : ((1ull << n) - 1ull);
-            m |= bits << (l - clo);
-        };
-        if (J.na > 0) add(J.a0l, J.a0h);
-        if (J.na > 1) add(J.a1l, J.a1h);
-        if (J.nb > 0) add(J.b0l, J.b0h);
-        if (J.nb > 1) add(J.b1l, J.b1h);
+    // touched chunks: each term's stored rows form up to two chunk ranges;
+    // the lanes walk their concatenation and drop chunks an earlier range
+    // already holds
+    int rl[4], rh[4];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int e1 = min(min(Arow[t] + R[t], Mv), Mr);
+        const bool p1 = act[t] && e1 > Arow[t];
+        rl[2 * t] = p1 ? Arow[t] >> 5 : 0;
+        rh[2 * t] = p1 ? ((e1 - 1) >> 5) + 1 : 0;
+        const int b1 = min(Arow[t] + R[t] - Mv, Mr);
+        const bool p2 = act[t] && b1 > 0;
+        rl[2 * t + 1] = 0;
+        rh[2 * t + 1] = p2 ? ((b1 - 1) >> 5) + 1 : 0;
     }
-    J.cmask = m;
+    const int p1 = rh[0] - rl[0];
+    const int p2 = p1 + rh[1] - rl[1];
+    const int p3 = p2 + rh[2] - rl[2];
+    const int total = p3 + rh[3] - rl[3];
+    int count = 0;
+    for (int base = 0; base < total; base += 32) {
+        const int idx = base + lane;
+        const int r = idx < p1 ? 0 : idx < p2 ? 1 : idx < p3 ? 2 : 3;
+        const int c = r == 0 ? rl[0] + idx : r == 1 ? rl[1] + idx - p1
+                    : r == 2 ? rl[2] + idx - p2 : rl[3] + idx - p3;
+        bool dup = (r > 0 && c >= rl[0] && c < rh[0]);
+        dup |= (r > 1 && c >= rl[1] && c < rh[1]);
+        dup |= (r > 2 && c >= rl[2] && c < rh[2]);
+        const bool keep = idx < total && !dup;
+        const unsigned ball = __ballot_sync(FULL, keep);
+        if (keep) clist[count + __popc(ball & ((1u << lane) - 1u))] = (unsigned short)c;
+        count += __popc(ball);
+    }
+    if (lane == 0) {
+        VJob J;
+        J.act0 = act[0];
+        J.act1 = act[1];
+        J.Arow0 = Arow[0];
+        J.Arow1 = Arow[1];
+        J.R0 = R[0];
+        J.R1 = R[1];
+        J.Acol0 = Acol[0];
+        J.Acol1 = Acol[1];
+        J.C0 = Cc[0];
+        J.C1 = Cc[1];
+        J.qb0 = qb[0];
+        J.qb1 = qb[1];
+        J.dq0 = dq[0];
+        J.dq1 = dq[1];
+        J.nstart = nstart;
+        J.cnt = cnt;
+        J.tile0 = tile[0];
+        J.tile1 = tile[1];
+        J.nlist = count;
+        J.pad[0] = J.pad[1] = J.pad[2] = 0;
+        *out = J;
+    }
 }
 
-__device__ __forceinline__ bool chunk_touched(const DictJob& J, int c) {
-    if (!J.cwide) {
-        const int d = c - J.cbase;
-        return d >= 0 && d < 64 && ((J.cmask >> d) & 1ull);
-    }
-    return in_ranges(J, c);
+// per-term quantities of one frame: the tile column's first entry and the
+// weight c e^{i 2 pi q / M_u} (zero when the column misses the frame)
+__device__ __forceinline__ void term_frame(int act, int Acol, int C, int R, int qb, int dq,
+                                           long long tile, int n, int Nv, int Mu, int Mumask,
+                                           const float2* cis_u, float2 c, float2& w,
+                                           long long& tbase) {
+    int cc = n - Acol;
+    cc += cc < 0 ? Nv : 0;
+    const bool hit = act && cc < C;
+    int q;
+    if (Mumask) q = (int)(((unsigned)qb + (unsigned)cc * (unsigned)dq) & (unsigned)Mumask);
+    else q = (int)(((long long)qb + (long long)cc * dq) % Mu);
+    w = hit ? cmul(c, cis_u[hit ? q : 0]) : make_float2(0.f, 0.f);
+    tbase = tile + (long long)cc * R;
+    if (!hit) tbase = -1;
 }
 
 template <int NT>
@@ -284,14 +259,18 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     __shared__ DevSig S;
     __shared__ DevDict sd[MAXW];
     __shared__ DevPair sp[MAXW * MAXW];
+    __shared__ VJob vj[MAXW];
     __shared__ int sstop[2];        // stop decision per iteration parity
     __shared__ int ltb[MAXW + 1];   // local top-level base per dictionary
+    __shared__ int clo[MAXW + 1];   // chunk-list base per dictionary
+    __shared__ int ndirty;          // dirty top-level groups this iteration
     __shared__ Entry wsel[NWARPS];  // per-warp bests of the scan
     __shared__ __align__(16) Entry cand[2][16];      // CTA bests of the cluster, per parity
     __shared__ __align__(16) int tmsg[2][4];         // time-limit message of CTA 0, per parity
     __shared__ __align__(8) unsigned long long xbar[2];  // exchange barriers, per parity
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = CS > 1 ? (int)cluster.block_rank() : 0;
+    const int cs_sh = __ffs(CS) - 1;
     DevSig& Sg = sigs[order[blockIdx.x / CS]];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     {
@@ -309,15 +288,19 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(xb1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         tmsg[0][0] = tmsg[1][0] = 0;
+        ndirty = 0;
     }
     __syncthreads();
     if (tid == 0) {
-        int b = 0;
+        int b = 0, c = 0;
         for (int w = 0; w < W; ++w) {
             ltb[w] = b;
             b += CS > 1 ? (int)(S.N[w] / CS) : S.tbase[w + 1] - S.tbase[w];
+            clo[w] = c;
+            c += (P.d[w].nch + 7) & ~7;
         }
         ltb[W] = b;
+        clo[W] = c;
     }
     __syncthreads();
     const int T = ltb[W];
@@ -325,7 +308,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     DevClass* scls = reinterpret_cast<DevClass*>(top + T);
     float2* sgam = reinterpret_cast<float2*>(scls + P.ncls);
     float2* scis = sgam + P.ngam;
-    unsigned char* tdirty = reinterpret_cast<unsigned char*>(scis + P.ncis);
+    unsigned* dbits = reinterpret_cast<unsigned*>(scis + P.ncis);  // dirty groups, one bit each
+    unsigned short* dlist = reinterpret_cast<unsigned short*>(dbits + ((T + 31) >> 5));
+    unsigned short* chl = dlist + ((T + 7) & ~7);  // touched-chunk lists
 
     for (int i = tid; i < P.ncls; i += NT) scls[i] = P.cls[i];
     for (int i = tid; i < P.ngam; i += NT) sgam[i] = P.gam[i];
@@ -339,7 +324,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
             for (int i = tid; i < te - tb; i += NT) top[tb + i] = src[i];
         }
     }
-    for (int i = tid; i < T; i += NT) tdirty[i] = 0;
+    for (int i = tid; i < ((T + 31) >> 5); i += NT) dbits[i] = 0u;
+    // dictionary bases of the flat index, one per lane (lane w < W)
+    const unsigned fb_l = lane < W ? S.fbase[lane] : 0xffffffffu;
 
     long long k = S.k;
     // FP64 work stays in one thread (the FP64 pipe is narrow on this part):
@@ -373,9 +360,6 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     // every CTA's barriers are initialised before anyone sends
     if (CS > 1) cluster.sync(); else __syncthreads();
 
-    // warp -> dictionary service: warp w serves v = w mod W as its slot w / W
-    // of nserve(v) warps (or, with fewer warps than dictionaries, v = w,
-    // w + NWARPS, ...)
     unsigned long long it = 0;  // iteration counter (exchange parities)
     for (;;) {
         const int par = (int)(it & 1);
@@ -454,14 +438,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         if (stop) break;
 
         const unsigned flat = 0xffffffffu - (unsigned)(best.key & 0xffffffffull);
-        int u = 0;
-        while (u + 1 < W && S.fbase[u + 1] <= flat) ++u;
-        const unsigned rel = flat - S.fbase[u];
-        const int j = (int)(rel >> sd[u].msh);
-        const int kk = (int)(rel & ((1u << sd[u].msh) - 1u));
+        // dictionary of the flat index: the number of bases w >= 1 at or below it
+        const int u = __popc(__ballot_sync(FULL, lane > 0 && lane < W && flat >= fb_l));
+        const unsigned rel = flat - __shfl_sync(FULL, fb_l, u);
+        const int msh = sd[u].msh;
+        const int j = (int)(rel >> msh);
+        const int kk = (int)(rel & ((1u << msh) - 1u));
         const int Mu = sd[u].M;
-        const int Mumask = sd[u].Mmask;
-        const float2* cis_u = scis + sd[u].cis_off;
         const bool edge = (kk == 0) || (2 * kk == Mu);
         // eqs. dualatprod / projenfaster: coefficient and energy drop in FP32
         // (gamma is zero away from m = 0 and m = M/2), E accumulated in FP64
@@ -507,164 +490,154 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
             sstop[(k + 1) & 1] = s1;
         }
         ++k;
-        const float2 c_main = make_float2(cx, cy), c_conj = make_float2(cx, -cy);
 
-        // ---- 3. frame jobs: each warp serves its dictionaries ---------------
-        // warp w serves dictionary w mod W as slot w / W of the warps that
-        // serve it; with fewer warps than dictionaries it serves w, w +
-        // NWARPS, ... alone
-        const int v_first = NWARPS >= W ? warp % W : warp;
-        const int v_step = NWARPS >= W ? W : NWARPS;
-        const int slot = NWARPS >= W ? warp / W : 0;
-        for (int v = v_first; v < W; v += v_step) {
-            const int nserve = NWARPS >= W ? (NWARPS / W + (v < NWARPS % W ? 1 : 0)) : 1;
-            DictJob J;
-            dict_job(sd, sp, scls, W, S, u, kk, j, edge, v, rank, CS, J);
-            const DevDict& Dv = sd[v];
-            const int Nv = (int)S.N[v];
-            for (int f = slot; f < J.cnt; f += nserve) {
+        // ---- 3. per-dictionary update descriptors ---------------------------
+        for (int v = warp; v < W; v += NWARPS)
+            build_vjob(sd, sp, scls, W, S, u, kk, j, edge, v, rank, CS, cs_sh, lane, &vj[v],
+                       chl + clo[v]);
+        __syncthreads();
+
+        // ---- 4. frame jobs, dealt from one flat index -----------------------
+        {
+            const float2 c_main = make_float2(cx, cy), c_conj = make_float2(cx, -cy);
+            const int Mumask = sd[u].Mmask;
+            const float2* cis_u = scis + sd[u].cis_off;
+            // inclusive prefix of the job counts, lane w holding dictionary w's
+            int pre = lane < W ? vj[lane].cnt : 0;
+#pragma unroll
+            for (int o = 1; o < MAXW; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, pre, o);
+                if (lane >= o) pre += y;
+            }
+            const int njobs = __shfl_sync(FULL, pre, W - 1);
+            for (int g = warp; g < njobs; g += NWARPS) {
+                const int v = __popc(__ballot_sync(FULL, lane < W && g >= pre));
+                const int f = g - (v > 0 ? __shfl_sync(FULL, pre, (v + 31) & 31) : 0);
+                const VJob& J = vj[v];
+                const DevDict& Dv = sd[v];
+                const int Nv = (int)S.N[v];
+                const int Mv = Dv.M, Mr = Dv.Mr, nch = Dv.nch;
                 int n = J.nstart + f * CS;
                 n -= (n >= Nv) ? Nv : 0;
                 n -= (n >= Nv) ? Nv : 0;
-                // level-0 entries of the whole frame (untouched chunks keep theirs)
-                const Entry* l0row = S.l0[v] + (long long)n * Dv.nch;
+                // level-0 entries of the whole frame (touched ones are replaced)
+                Entry* l0row = S.l0[v] + (long long)n * nch;
                 Entry l0v[MAXL0];
 #pragma unroll
                 for (int q = 0; q < MAXL0; ++q) {
                     const int c = lane + 32 * q;
-                    if (c < Dv.nch) l0v[q] = l0row[c];
+                    if (c < nch) {
+                        l0v[q] = l0row[c];
+                    } else {
+                        l0v[q].key = 0ull;
+                        l0v[q].val = make_float2(0.f, 0.f);
+                    }
                 }
                 float2* prow = S.plane[v] + (long long)n * Dv.Mrp;
-                const float2 w0 = J.t0.active ? cmul(c_main, cis_u[term_q(J.t0, n, Nv, Dv.a, Mu, Mumask)])
-                                              : make_float2(0.f, 0.f);
-                const float2 w1 = J.t1.active ? cmul(c_conj, cis_u[term_q(J.t1, n, Nv, Dv.a, Mu, Mumask)])
-                                              : make_float2(0.f, 0.f);
-                Entry fmax;
-                fmax.key = 0;
-                fmax.val = make_float2(0.f, 0.f);
-                // touched chunks, CB at a time, lowest first (bit mask; a set
-                // wider than 64 chunks is walked chunk by chunk)
-                unsigned long long mrest = J.cmask;
-                int wc = J.cbase;
-                for (;;) {
-                    int chunk[CB];
-                    int cnt = 0;
-#pragma unroll
-                    for (int q = 0; q < CB; ++q) {
-                        chunk[q] = -1;
-                        if (!J.cwide) {
-                            if (mrest) {
-                                const int b = __ffsll((long long)mrest) - 1;
-                                mrest &= mrest - 1ull;
-                                chunk[q] = J.cbase + b;
-                            }
-                        } else {
-                            while (wc < J.cend && !in_ranges(J, wc)) ++wc;
-                            if (wc < J.cend) chunk[q] = wc++;
-                        }
-                        cnt += chunk[q] >= 0 ? 1 : 0;
-                    }
-                    if (cnt == 0) break;
+                float2 w0, w1;
+                long long tb0, tb1;
+                term_frame(J.act0, J.Acol0, J.C0, J.R0, J.qb0, J.dq0, J.tile0, n, Nv, Mu, Mumask,
+                           cis_u, c_main, w0, tb0);
+                term_frame(J.act1, J.Acol1, J.C1, J.R1, J.qb1, J.dq1, J.tile1, n, Nv, Mu, Mumask,
+                           cis_u, c_conj, w1, tb1);
+                const unsigned short* lst = chl + clo[v];
+                const unsigned fn = S.fbase[v] + ((unsigned)n << Dv.msh);
+                for (int b0 = 0; b0 < J.nlist; b0 += CB) {
+                    int cq[CB];
                     float2 val[CB], h0[CB], h1[CB];
-                    bool hit0[CB], hit1[CB];
+                    bool hit[CB];
 #pragma unroll
                     for (int q = 0; q < CB; ++q) {
-                        hit0[q] = hit1[q] = false;
-                        if (chunk[q] >= 0) {
-                            const int m = chunk[q] * CHUNK + lane;
-                            val[q] = prow[m];
-                            int off;
-                            if (m < Dv.Mr) {
-                                if (term_hit(J.t0, m, n, Dv.M, Nv, &off)) {
-                                    hit0[q] = true;
-                                    h0[q] = __ldg(tiles + J.t0.tile + off);
-                                }
-                                if (term_hit(J.t1, m, n, Dv.M, Nv, &off)) {
-                                    hit1[q] = true;
-                                    h1[q] = __ldg(tiles + J.t1.tile + off);
-                                }
-                            }
-                        }
+                        cq[q] = b0 + q < J.nlist ? (int)lst[b0 + q] : -1;
+                        const int m = cq[q] * CHUNK + lane;
+                        const bool ok = cq[q] >= 0;
+                        val[q] = ok ? prow[ok ? m : 0] : make_float2(0.f, 0.f);
+                        int i0 = m - J.Arow0;
+                        i0 += i0 < 0 ? Mv : 0;
+                        int i1 = m - J.Arow1;
+                        i1 += i1 < 0 ? Mv : 0;
+                        const bool s0 = ok && m < Mr && tb0 >= 0 && i0 < J.R0;
+                        const bool s1 = ok && m < Mr && tb1 >= 0 && i1 < J.R1;
+                        h0[q] = s0 ? __ldg(tiles + tb0 + i0) : make_float2(0.f, 0.f);
+                        h1[q] = s1 ? __ldg(tiles + tb1 + i1) : make_float2(0.f, 0.f);
+                        hit[q] = s0 || s1;
                     }
 #pragma unroll
                     for (int q = 0; q < CB; ++q) {
-                        if (chunk[q] < 0) continue;
-                        const int m = chunk[q] * CHUNK + lane;
+                        const int m = cq[q] * CHUNK + lane;
                         float2 x2 = val[q];
-                        if (hit0[q]) {
-                            const float2 d = cmul(w0, h0[q]);
-                            x2.x -= d.x;
-                            x2.y -= d.y;
-                        }
-                        if (hit1[q]) {
-                            const float2 d = cmul(w1, h1[q]);
-                            x2.x -= d.x;
-                            x2.y -= d.y;
-                        }
-                        if (hit0[q] || hit1[q]) prow[m] = x2;
+                        const float2 d0 = cmul(w0, h0[q]);
+                        x2.x -= d0.x;
+                        x2.y -= d0.y;
+                        const float2 d1 = cmul(w1, h1[q]);
+                        x2.x -= d1.x;
+                        x2.y -= d1.y;
+                        if (hit[q]) prow[m] = x2;
                         Entry e;
                         e.val = x2;
-                        e.key = (m < Dv.Mr) ? make_key_sel(x2, S.fbase[v] + ((unsigned)n << Dv.msh) + m,
-                                                            m, Dv, sgam, P.pedantic)
-                                            : 0ull;
+                        e.key = (cq[q] >= 0 && m < Mr)
+                                    ? make_key_sel(x2, fn + m, m, Dv, sgam, P.pedantic)
+                                    : 0ull;
                         const Entry rr = warp_max_entry(e);
-                        if (lane == 0) S.l0[v][(long long)n * Dv.nch + chunk[q]] = rr;
-                        if (rr.key > fmax.key) fmax = rr;
+                        if (cq[q] >= 0) {
+                            if (lane == q) l0row[cq[q]] = rr;
+#pragma unroll
+                            for (int s = 0; s < MAXL0; ++s)
+                                if (cq[q] == lane + 32 * s) l0v[s] = rr;
+                        }
                     }
                 }
-                // frame maximum: untouched chunks from level 0, touched ones recomputed
-                Entry b = fmax;
+                // frame maximum over the (updated) level-0 entries
+                Entry fb = l0v[0];
 #pragma unroll
-                for (int q = 0; q < MAXL0; ++q) {
-                    const int cq = lane + 32 * q;
-                    if (cq < Dv.nch && !chunk_touched(J, cq) && l0v[q].key > b.key) b = l0v[q];
+                for (int s = 1; s < MAXL0; ++s)
+                    if (l0v[s].key > fb.key) fb = l0v[s];
+                if (nch > 32 * MAXL0) {
+                    __syncwarp();  // this warp's level-0 stores are visible to its loads
+                    for (int c = lane + 32 * MAXL0; c < nch; c += 32) {
+                        const Entry e = l0row[c];
+                        if (e.key > fb.key) fb = e;
+                    }
                 }
-                for (int cq = lane + 32 * MAXL0; cq < Dv.nch; cq += 32) {
-                    if (chunk_touched(J, cq)) continue;
-                    const Entry e = l0row[cq];
-                    if (e.key > b.key) b = e;
-                }
-                const Entry fr = warp_max_entry(b);
+                const Entry fr = warp_max_entry(fb);
                 if (lane == 0) {
                     S.l1[v][n] = fr;
-                    if (CS > 1) top[ltb[v] + n / CS] = fr;
-                    else if (S.gshift == 0) top[ltb[v] + n] = fr;
-                    else tdirty[ltb[v] + (n >> S.gshift)] = 1;
+                    if (CS > 1) {
+                        top[ltb[v] + (n >> cs_sh)] = fr;
+                    } else if (S.gshift == 0) {
+                        top[ltb[v] + n] = fr;
+                    } else {
+                        const int gi = ltb[v] + (n >> S.gshift);
+                        const unsigned bit = 1u << (gi & 31);
+                        if (!(atomicOr(&dbits[gi >> 5], bit) & bit))
+                            dlist[atomicAdd(&ndirty, 1)] = (unsigned short)gi;
+                    }
                 }
             }
-            if (NWARPS >= W) break;  // one dictionary per warp
         }
         __syncthreads();
 
-        // ---- level 2 (groups) of touched frames (single-CTA launches) -------
+        // ---- 5. level 2 (groups) of touched frames (single-CTA launches) ----
         if (CS == 1 && S.gshift > 0) {
-            for (int base = warp * 32; base < T; base += NWARPS * 32) {
-                const int i = base + lane;
-                unsigned ball = __ballot_sync(FULL, i < T && tdirty[i]);
-                while (ball) {
-                    const int bb = __ffs(ball) - 1;
-                    ball &= ball - 1;
-                    const int gi = base + bb;
-                    int w = 0;
-                    while (w + 1 < W && S.tbase[w + 1] <= gi) ++w;
-                    const int f0 = (gi - S.tbase[w]) << S.gshift;
-                    const int f1 = min(f0 + (1 << S.gshift), (int)S.N[w]);
-                    Entry m2;
-                    m2.key = 0;
-                    m2.val = make_float2(0.f, 0.f);
-                    for (int f = f0 + lane; f < f1; f += 32) {
-                        const Entry e = S.l1[w][f];
-                        if (e.key > m2.key) m2 = e;
-                    }
-                    const Entry gr = warp_max_entry(m2);
-                    if (lane == 0) {
-                        S.grp[gi] = gr;
-                        top[gi] = gr;
-                        tdirty[gi] = 0;
-                    }
+            const int nd = ndirty;
+            for (int i = tid; i < nd; i += NT) {
+                const int gi = dlist[i];
+                int w = 0;
+                while (w + 1 < W && S.tbase[w + 1] <= gi) ++w;
+                const int f0 = (gi - S.tbase[w]) << S.gshift;
+                const int f1 = min(f0 + (1 << S.gshift), (int)S.N[w]);
+                const Entry* l1 = S.l1[w];
+                Entry m2 = l1[f0];
+                for (int f = f0 + 1; f < f1; ++f) {
+                    const Entry e = l1[f];
+                    if (e.key > m2.key) m2 = e;
                 }
+                S.grp[gi] = m2;
+                top[gi] = m2;
+                dbits[gi >> 5] = 0u;
             }
             __syncthreads();
+            if (tid == 0) ndirty = 0;
         }
         ++it;
     }
@@ -746,9 +719,14 @@ int max_clusters(int cs, size_t smem) {
 
 }  // namespace
 
+// dynamic shared memory of the loop: top level, class descriptors, <d, conj d>
+// and modulation tables, dirty-group bits and list, touched-chunk lists
 size_t mp_loop_smem_bytes(const DevPlan& P, int T, int, int) {
+    size_t chl = 0;
+    for (int w = 0; w < P.W; ++w) chl += (size_t)((P.d[w].nch + 7) & ~7);
     size_t b = (size_t)T * sizeof(Entry) + (size_t)P.ncls * sizeof(DevClass) +
-               (size_t)(P.ngam + P.ncis) * sizeof(float2) + (size_t)T;
+               (size_t)(P.ngam + P.ncis) * sizeof(float2) + 4 * (size_t)((T + 31) >> 5) +
+               2 * (size_t)((T + 7) & ~7) + 2 * chl;
     return (b + 15) & ~(size_t)15;
 }
 
