@@ -168,8 +168,8 @@ int mp_get_status(mp_state* state, int64_t* n_atoms, int* stop_reason, double* f
 int mp_state_set_time_limit(mp_state* state, double seconds);
 
 /*
- * Launch shape of the MP loop (tuning): threads per CTA (128, 256, 512 or
- * 1024) and CTAs per signal (thread-block cluster of 1, 2, 4, 8 or 16; more
+ * Launch shape of the MP loop (tuning): threads per CTA (128, 256 or 512)
+ * and CTAs per signal (thread-block cluster of 1, 2, 4, 8 or 16; more
  * than one needs every N_w = L/a_w divisible by it).  The default is chosen
  * from the number of signals; threads = cluster = 0 restores it.  Returns
  * MP_EINVAL for a shape this state cannot run.  mp_state_get_launch reports

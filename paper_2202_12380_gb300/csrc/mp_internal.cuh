@@ -65,6 +65,7 @@ struct DevPlan {
     int ngam;  // entries of the compact <d, conj d> pool
     int ncis;  // entries of the modulation tables
     int pedantic;  // selection by the pair energy drop (MP_PEDANTIC)
+    int pow2;      // every M_w and a_w is a power of two
     DevDict d[MAXW];
     DevPair p[MAXW * MAXW];
     const DevClass* cls;

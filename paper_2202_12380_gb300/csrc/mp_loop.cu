@@ -118,31 +118,45 @@ __device__ __forceinline__ bool xbar_try(unsigned addr, unsigned parity) {
 }
 
 // Dictionary v's update for the selected atom (u, k, j), built by one warp
-// (every lane computes the scalars; the lanes split the chunk list).
+// (every lane computes the scalars; the lanes split the chunk list).  POW2:
+// every M and a is a power of two, so the class, row and modulation indices
+// are shifts and masks.  tmk receives, per lane, which of the chunks
+// lane + 32 s (s < MAXL0) are touched.
+template <bool POW2>
 __device__ __forceinline__ void build_vjob(const DevDict* sd, const DevPair* sp,
                                            const DevClass* scls, int W, const DevSig& S, int u,
                                            int kk, int j, bool edge, int v, int rank, int CS,
                                            int cs_sh, int lane, VJob* out,
-                                           unsigned short* clist) {
+                                           unsigned short* clist, unsigned char* tmk) {
     const DevDict& Du = sd[u];
     const DevDict& Dv = sd[v];
     const DevPair& PR = sp[u * W + v];
     const int Mu = Du.M, Mumask = Du.Mmask, au = Du.a;
     const int Mv = Dv.M, Mr = Dv.Mr, av = Dv.a;
     const int Nv = (int)S.N[v];
-    const int ct = PR.rt_sh >= 0 ? (j & (PR.rt - 1)) : j % PR.rt;
-    const int base_n = PR.aratio ? j * PR.aratio
-                                 : (PR.rt_sh >= 0 ? j >> PR.rt_sh : (j - ct) / PR.rt);
+    int ct, base_n;
+    if (POW2) {
+        ct = j & (PR.rt - 1);
+        base_n = PR.aratio ? j * PR.aratio : j >> PR.rt_sh;
+    } else {
+        ct = j % PR.rt;
+        base_n = PR.aratio ? j * PR.aratio : (j - ct) / PR.rt;
+    }
     int act[2], Arow[2], R[2], Acol[2], Cc[2], a0[2], qb[2], dq[2];
     long long tile[2];
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
         const int kt = t ? Mu - kk : kk;
-        const int cf = PR.rf_sh >= 0 ? (kt & (PR.rf - 1)) : kt % PR.rf;
+        int cf, base_m;
+        if (POW2) {
+            cf = kt & (PR.rf - 1);
+            base_m = PR.mratio ? kt * PR.mratio : kt >> PR.rf_sh;
+        } else {
+            cf = kt % PR.rf;
+            base_m = PR.mratio ? kt * PR.mratio : (kt - cf) / PR.rf;
+        }
         const DevClass C = scls[PR.cls_base + cf * PR.rt + ct];
-        const int base_m = PR.mratio ? kt * PR.mratio
-                                     : (PR.rf_sh >= 0 ? kt >> PR.rf_sh : (kt - cf) / PR.rf);
-        Arow[t] = wrap2(base_m + C.i_lo, Mv);
+        Arow[t] = POW2 ? ((base_m + C.i_lo) & Dv.Mmask) : wrap2(base_m + C.i_lo, Mv);
         R[t] = C.R;
         // any stored row (0 .. M_v/2) inside [Arow, Arow + R) mod M_v ?
         act[t] = (t == 0 || !edge) && C.R > 0 && (Arow[t] < Mr || Arow[t] + C.R > Mv);
@@ -150,7 +164,7 @@ __device__ __forceinline__ void build_vjob(const DevDict* sd, const DevPair* sp,
         Acol[t] = wrap2(a0[t], Nv);
         Cc[t] = C.C;
         const int tau0 = C.c_lo * av - ct * au;
-        if (Mumask) {
+        if (POW2) {
             qb[t] = (int)(((unsigned)kt * (unsigned)tau0) & (unsigned)Mumask);
             dq[t] = (int)(((unsigned)kt * (unsigned)av) & (unsigned)Mumask);
         } else {
@@ -187,6 +201,16 @@ __device__ __forceinline__ void build_vjob(const DevDict* sd, const DevPair* sp,
         rl[2 * t + 1] = 0;
         rh[2 * t + 1] = p2 ? ((b1 - 1) >> 5) + 1 : 0;
     }
+    unsigned mk = 0;
+#pragma unroll
+    for (int s = 0; s < MAXL0; ++s) {
+        const int c = lane + 32 * s;
+        bool in = false;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) in |= c >= rl[r] && c < rh[r];
+        mk |= in ? (1u << s) : 0u;
+    }
+    tmk[lane] = (unsigned char)mk;
     const int p1 = rh[0] - rl[0];
     const int p2 = p1 + rh[1] - rl[1];
     const int p3 = p2 + rh[2] - rl[2];
@@ -231,6 +255,24 @@ __device__ __forceinline__ void build_vjob(const DevDict* sd, const DevPair* sp,
     }
 }
 
+// two warp-wide max reductions run side by side (independent chains)
+__device__ __forceinline__ void warp_max_entry2(Entry& a, Entry& b) {
+    const unsigned ha = (unsigned)(a.key >> 32), la = (unsigned)a.key;
+    const unsigned hb = (unsigned)(b.key >> 32), lb = (unsigned)b.key;
+    const unsigned mha = __reduce_max_sync(FULL, ha);
+    const unsigned mhb = __reduce_max_sync(FULL, hb);
+    const unsigned mla = __reduce_max_sync(FULL, ha == mha ? la : 0u);
+    const unsigned mlb = __reduce_max_sync(FULL, hb == mhb ? lb : 0u);
+    const unsigned sa = __ffs(__ballot_sync(FULL, ha == mha && la == mla)) - 1;
+    const unsigned sb = __ffs(__ballot_sync(FULL, hb == mhb && lb == mlb)) - 1;
+    a.key = ((unsigned long long)mha << 32) | mla;
+    b.key = ((unsigned long long)mhb << 32) | mlb;
+    const float ax = __shfl_sync(FULL, a.val.x, sa), ay = __shfl_sync(FULL, a.val.y, sa);
+    const float bx = __shfl_sync(FULL, b.val.x, sb), by = __shfl_sync(FULL, b.val.y, sb);
+    a.val = make_float2(ax, ay);
+    b.val = make_float2(bx, by);
+}
+
 // per-term quantities of one frame: the tile column's first entry and the
 // weight c e^{i 2 pi q / M_u} (zero when the column misses the frame)
 __device__ __forceinline__ void term_frame(int act, int Acol, int C, int R, int qb, int dq,
@@ -248,7 +290,7 @@ __device__ __forceinline__ void term_frame(int act, int Acol, int C, int R, int 
     if (!hit) tbase = -1;
 }
 
-template <int NT>
+template <int NT, bool POW2>
 __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     k_mp_loop(DevPlan P, DevSig* __restrict__ sigs, const int* __restrict__ order,
               long long kmax, double thr_scale, long long budget_ns, int CS, long long reset_it,
@@ -260,6 +302,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     __shared__ DevDict sd[MAXW];
     __shared__ DevPair sp[MAXW * MAXW];
     __shared__ VJob vj[MAXW];
+    __shared__ unsigned char tmk[MAXW][32];  // touched chunks lane + 32 s, per lane
     __shared__ int sstop[2];        // stop decision per iteration parity
     __shared__ int ltb[MAXW + 1];   // local top-level base per dictionary
     __shared__ int clo[MAXW + 1];   // chunk-list base per dictionary
@@ -493,8 +536,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
 
         // ---- 3. per-dictionary update descriptors ---------------------------
         for (int v = warp; v < W; v += NWARPS)
-            build_vjob(sd, sp, scls, W, S, u, kk, j, edge, v, rank, CS, cs_sh, lane, &vj[v],
-                       chl + clo[v]);
+            build_vjob<POW2>(sd, sp, scls, W, S, u, kk, j, edge, v, rank, CS, cs_sh, lane, &vj[v],
+                             chl + clo[v], tmk[v]);
         __syncthreads();
 
         // ---- 4. frame jobs, dealt from one flat index -----------------------
@@ -542,13 +585,19 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                            cis_u, c_conj, w1, tb1);
                 const unsigned short* lst = chl + clo[v];
                 const unsigned fn = S.fbase[v] + ((unsigned)n << Dv.msh);
+                const unsigned tm = tmk[v][lane];
+                // maximum of the touched chunks' new level-0 entries (uniform)
+                Entry tmax;
+                tmax.key = 0ull;
+                tmax.val = make_float2(0.f, 0.f);
                 for (int b0 = 0; b0 < J.nlist; b0 += CB) {
+                    const int nb = min(CB, J.nlist - b0);  // uniform
                     int cq[CB];
                     float2 val[CB], h0[CB], h1[CB];
                     bool hit[CB];
 #pragma unroll
                     for (int q = 0; q < CB; ++q) {
-                        cq[q] = b0 + q < J.nlist ? (int)lst[b0 + q] : -1;
+                        cq[q] = q < nb ? (int)lst[b0 + q] : -1;
                         const int m = cq[q] * CHUNK + lane;
                         const bool ok = cq[q] >= 0;
                         val[q] = ok ? prow[ok ? m : 0] : make_float2(0.f, 0.f);
@@ -562,6 +611,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                         h1[q] = s1 ? __ldg(tiles + tb1 + i1) : make_float2(0.f, 0.f);
                         hit[q] = s0 || s1;
                     }
+                    Entry e[CB];
 #pragma unroll
                     for (int q = 0; q < CB; ++q) {
                         const int m = cq[q] * CHUNK + lane;
@@ -573,25 +623,29 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                         x2.x -= d1.x;
                         x2.y -= d1.y;
                         if (hit[q]) prow[m] = x2;
-                        Entry e;
-                        e.val = x2;
-                        e.key = (cq[q] >= 0 && m < Mr)
-                                    ? make_key_sel(x2, fn + m, m, Dv, sgam, P.pedantic)
-                                    : 0ull;
-                        const Entry rr = warp_max_entry(e);
-                        if (cq[q] >= 0) {
-                            if (lane == q) l0row[cq[q]] = rr;
+                        e[q].val = x2;
+                        e[q].key = (cq[q] >= 0 && m < Mr)
+                                       ? make_key_sel(x2, fn + m, m, Dv, sgam, P.pedantic)
+                                       : 0ull;
+                    }
+                    // chunk maxima, two at a time; the second pair only when
+                    // the batch holds more than two chunks
+                    warp_max_entry2(e[0], e[1]);
+                    if (nb > 2) warp_max_entry2(e[2], e[3]);
 #pragma unroll
-                            for (int s = 0; s < MAXL0; ++s)
-                                if (cq[q] == lane + 32 * s) l0v[s] = rr;
+                    for (int q = 0; q < CB; ++q) {
+                        if (q < nb) {
+                            if (lane == q) l0row[cq[q]] = e[q];
+                            if (e[q].key > tmax.key) tmax = e[q];
                         }
                     }
                 }
-                // frame maximum over the (updated) level-0 entries
-                Entry fb = l0v[0];
+                // frame maximum: the touched chunks' new entries and the
+                // untouched chunks' stored ones
+                Entry fb = tmax;
 #pragma unroll
-                for (int s = 1; s < MAXL0; ++s)
-                    if (l0v[s].key > fb.key) fb = l0v[s];
+                for (int s = 0; s < MAXL0; ++s)
+                    if (!((tm >> s) & 1u) && l0v[s].key > fb.key) fb = l0v[s];
                 if (nch > 32 * MAXL0) {
                     __syncwarp();  // this warp's level-0 stores are visible to its loads
                     for (int c = lane + 32 * MAXL0; c < nch; c += 32) {
@@ -660,57 +714,51 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     }
 }
 
-template <int NT>
-cudaError_t launch_nt(const DevPlan& P, DevSig* d_sigs, const int* d_order, int nsig, long long kmax,
-                      double thr_scale, long long budget_ns, size_t smem, int cs, cudaStream_t st,
-                      long long reset_it, double reset_scale) {
-    cudaError_t e = cudaFuncSetAttribute(k_mp_loop<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    if (cs > 8) {
-        e = cudaFuncSetAttribute(k_mp_loop<NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
+using LoopKernel = void (*)(DevPlan, DevSig*, const int*, long long, double, long long, int,
+                           long long, double);
+
+// the loop instantiation for a CTA size (0 if unsupported)
+LoopKernel loop_kernel(int threads, bool pow2) {
+    switch (threads) {
+        case 512: return pow2 ? k_mp_loop<512, true> : k_mp_loop<512, false>;
+        case 256: return pow2 ? k_mp_loop<256, true> : k_mp_loop<256, false>;
+        case 128: return pow2 ? k_mp_loop<128, true> : k_mp_loop<128, false>;
+        default: return nullptr;
     }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(nsig * cs));
-    cfg.blockDim = dim3(NT);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_mp_loop<NT>, P, d_sigs, d_order, kmax, thr_scale, budget_ns, cs,
-                           reset_it, reset_scale);
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
 }
 
-template <int NT>
-int max_clusters(int cs, size_t smem) {
-    if (cs > 8 &&
-        cudaFuncSetAttribute(k_mp_loop<NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-            cudaSuccess)
-        return 0;
-    if (cudaFuncSetAttribute(k_mp_loop<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-        return 0;
+cudaLaunchConfig_t loop_config(int nsig, int threads, int cs, size_t smem, cudaStream_t st,
+                               cudaLaunchAttribute* attr) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)cs);
-    cfg.blockDim = dim3(NT);
+    cfg.gridDim = dim3((unsigned)(nsig * cs));
+    cfg.blockDim = dim3((unsigned)threads);
     cfg.dynamicSmemBytes = smem;
-    cudaLaunchAttribute attr[1];
+    cfg.stream = st;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)cs;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    return cfg;
+}
+
+cudaError_t prepare(LoopKernel kf, int cs, size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (cs > 8) e = cudaFuncSetAttribute(kf, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+int max_clusters(LoopKernel kf, int threads, int cs, size_t smem) {
+    if (!kf || prepare(kf, cs, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = loop_config(1, threads, cs, smem, 0, attr);
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k_mp_loop<NT>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, kf, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -731,13 +779,8 @@ size_t mp_loop_smem_bytes(const DevPlan& P, int T, int, int) {
 }
 
 int mp_loop_max_clusters(int threads, int cs, size_t smem) {
-    switch (threads) {
-        case 1024: return max_clusters<1024>(cs, smem);
-        case 512: return max_clusters<512>(cs, smem);
-        case 256: return max_clusters<256>(cs, smem);
-        case 128: return max_clusters<128>(cs, smem);
-        default: return 0;
-    }
+    // both instantiations have the same resources; the generic one stands in
+    return max_clusters(loop_kernel(threads, false), threads, cs, smem);
 }
 
 int mp_loop_threads(int nsig, int num_sms) {
@@ -748,7 +791,7 @@ int mp_loop_threads(int nsig, int num_sms) {
 
 // feasibility of a requested launch shape (threads per CTA, cluster size)
 bool mp_loop_shape_ok(const DevPlan& P, const DevSig* hs, int B, int threads, int c, size_t* smem) {
-    if (threads != 128 && threads != 256 && threads != 512 && threads != 1024) return false;
+    if (threads != 128 && threads != 256 && threads != 512) return false;
     if (c != 1 && c != 2 && c != 4 && c != 8 && c != 16) return false;
     if (c == 1) {
         int tmax = 1;
@@ -781,7 +824,7 @@ void mp_loop_shape(const DevPlan& P, const DevSig* hs, int B, int num_sms, int* 
     int nt_override = 0;
     if (const char* ov = getenv("MPGABOR_LOOP_THREADS")) {  // tuning overrides
         int t = atoi(ov);
-        if (t == 128 || t == 256 || t == 512 || t == 1024) nt_override = t;
+        if (t == 128 || t == 256 || t == 512) nt_override = t;
     }
     if (const char* ov = getenv("MPGABOR_CLUSTER")) {
         int t = atoi(ov);
@@ -822,17 +865,16 @@ cudaError_t launch_mp_loop(const DevPlan& P, DevSig* d_sigs, const int* d_order,
                            int threads, int cs, cudaStream_t st, long long reset_it,
                            double reset_scale) {
     if (nsig <= 0) return cudaSuccess;
-#define MPG_LAUNCH(NTV)                                                                        \
-    launch_nt<NTV>(P, d_sigs, d_order, nsig, kmax, thr_scale, budget_ns, smem, cs, st, reset_it, \
-                   reset_scale)
-    switch (threads) {
-        case 1024: return MPG_LAUNCH(1024);
-        case 512: return MPG_LAUNCH(512);
-        case 256: return MPG_LAUNCH(256);
-        case 128: return MPG_LAUNCH(128);
-        default: return cudaErrorInvalidValue;
-    }
-#undef MPG_LAUNCH
+    LoopKernel kf = loop_kernel(threads, P.pow2 != 0);
+    if (!kf) return cudaErrorInvalidValue;
+    cudaError_t e = prepare(kf, cs, smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = loop_config(nsig, threads, cs, smem, st, attr);
+    e = cudaLaunchKernelEx(&cfg, kf, P, d_sigs, d_order, kmax, thr_scale, budget_ns, cs, reset_it,
+                           reset_scale);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
 }
 
 }  // namespace mpg

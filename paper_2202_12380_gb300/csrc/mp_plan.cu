@@ -544,6 +544,9 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
         p->dp.g32 = p->d_g32;
         p->dp.cis = p->d_cis32;
         p->dp.pedantic = (flags & MP_PEDANTIC) ? 1 : 0;
+        p->dp.pow2 = 1;
+        for (int w = 0; w < W; ++w)
+            if ((M[w] & (M[w] - 1)) || (a[w] & (a[w] - 1))) p->dp.pow2 = 0;
     }
     for (int w = 0; w < W; ++w) {
         cudaFree(d_win[w]);
