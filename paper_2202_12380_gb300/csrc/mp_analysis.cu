@@ -165,52 +165,18 @@ __global__ void k_tree_build(DevPlan P, const DevSig* __restrict__ sigs, int nsi
     const long long n = gw - fprefix[s];
     const DevDict& D = P.d[dict];
     const float2* row = S.plane[dict] + n * D.Mrp;
-    Entry* l0 = S.l0[dict] + n * D.nch;
+    Key* l0 = S.l0[dict] + n * D.nch;
     const unsigned fb = S.fbase[dict] + ((unsigned)n << D.msh);
-    Entry best;
-    best.key = 0;
-    best.val = make_float2(0.f, 0.f);
+    Key best = 0ull;
     for (int ch = 0; ch < D.nch; ++ch) {
-        int m = ch * CHUNK + lane;
-        Entry e;
-        e.val = row[m];
-        e.key = (m < D.Mr) ? make_key_sel(e.val, fb + m, m, D, P.gam, P.pedantic) : 0ull;
-        Entry r = warp_max_entry(e);
+        const int m = ch * CHUNK + lane;
+        const float2 v = row[m];
+        const Key k = (m < D.Mr) ? make_key_sel(v, fb + m, m, D, P.gam, P.pedantic) : 0ull;
+        const Key r = warp_max_key(k);
         if (lane == 0) l0[ch] = r;
-        if (r.key > best.key) best = r;
+        best = r > best ? r : best;
     }
     if (lane == 0) S.l1[dict][n] = best;
-}
-
-// level 2: groups of 2^gshift frames (signals whose frames exceed the
-// on-chip top level), one warp per group
-__global__ void k_group_build(const DevSig* __restrict__ sigs, int nsig,
-                              const int* __restrict__ gprefix, long long total, int W,
-                              int flagged) {
-    long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (gw >= total) return;
-    const int lane = threadIdx.x & 31;
-    int lo = 0, hi = nsig - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (gprefix[mid] <= gw) lo = mid; else hi = mid - 1;
-    }
-    const DevSig& S = sigs[lo];
-    if (flagged && !S.reanalyze) return;
-    const int g = (int)(gw - gprefix[lo]);
-    int w = 0;
-    while (w + 1 < W && S.tbase[w + 1] <= g) ++w;
-    const long long f0 = (long long)(g - S.tbase[w]) << S.gshift;
-    const long long f1 = min(f0 + (1ll << S.gshift), S.N[w]);
-    Entry best;
-    best.key = 0;
-    best.val = make_float2(0.f, 0.f);
-    for (long long f = f0 + lane; f < f1; f += 32) {
-        Entry e = S.l1[w][f];
-        if (e.key > best.key) best = e;
-    }
-    Entry r = warp_max_entry(best);
-    if (lane == 0) S.grp[g] = r;
 }
 
 // reset pass, one block per signal: r = x - y and E = E_out = ||r||^2
@@ -276,13 +242,5 @@ cudaError_t launch_tree_build(const DevPlan& P, const DevSig* d_sigs, int nsig,
     return cudaGetLastError();
 }
 
-cudaError_t launch_group_build(const DevSig* d_sigs, int nsig, const int* d_group_prefix,
-                               long long total_groups, int W, cudaStream_t st, int flagged) {
-    if (total_groups <= 0) return cudaSuccess;
-    const int wpb = 8;
-    k_group_build<<<(unsigned)((total_groups + wpb - 1) / wpb), wpb * 32, 0, st>>>(
-        d_sigs, nsig, d_group_prefix, total_groups, W, flagged);
-    return cudaGetLastError();
-}
 
 }  // namespace mpg

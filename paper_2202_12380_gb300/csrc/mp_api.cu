@@ -41,9 +41,6 @@ struct mp_state {
     long long total_tiles[MAXW];
     long long* d_frame_prefix[MAXW];
     long long total_frames[MAXW];
-    int* d_group_prefix;
-    long long total_groups;
-    int Tmax;
     size_t smem;             // MP launch shape (see mp_loop_shape)
     int threads, cs;
     long long cap;           // atom capacity per signal
@@ -87,7 +84,6 @@ void state_free(mp_state* s) {
         if (s->d_tile_prefix[w]) cudaFree(s->d_tile_prefix[w]);
         if (s->d_frame_prefix[w]) cudaFree(s->d_frame_prefix[w]);
     }
-    if (s->d_group_prefix) cudaFree(s->d_group_prefix);
     if (s->d_atoms) cudaFree(s->d_atoms);
     if (s->d_errs) cudaFree(s->d_errs);
     if (s->d_scalar) cudaFree(s->d_scalar);
@@ -154,7 +150,6 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
     s->d_sigs = nullptr;
     s->d_order = nullptr;
     s->pool = nullptr;
-    s->d_group_prefix = nullptr;
     s->d_atoms = nullptr;
     s->d_errs = nullptr;
     s->d_scalar = nullptr;
@@ -162,12 +157,10 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
     s->time_limit_s = 0.0;
     s->reset_it = 0;
     s->reset_db = 0.0;
-    s->Tmax = 1;
     const int W = p->W;
     // layout of every signal inside one pool
     size_t off = 0;
-    std::vector<size_t> o_plane(B * W), o_l0(B * W), o_l1(B * W), o_grp(B), o_x(B), o_r(B),
-        o_y(B);
+    std::vector<size_t> o_plane(B * W), o_l0(B * W), o_l1(B * W), o_x(B), o_r(B), o_y(B);
     for (int b = 0; b < B; ++b) {
         DevSig& S = s->hs[b];
         memset(&S, 0, sizeof(S));
@@ -184,30 +177,11 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
             o_plane[b * W + w] = off;
             off = align256(off + sizeof(float2) * S.N[w] * D.Mrp);
             o_l0[b * W + w] = off;
-            off = align256(off + sizeof(Entry) * S.N[w] * D.nch);
+            off = align256(off + sizeof(Key) * S.N[w] * D.nch);
             o_l1[b * W + w] = off;
-            off = align256(off + sizeof(Entry) * S.N[w]);
+            off = align256(off + sizeof(Key) * S.N[w]);
         }
         S.fbase[W] = fb;
-        int gs = 0;
-        if (F > TOPCAP) {
-            for (gs = 1; gs < 40; ++gs) {
-                long long T = 0;
-                for (int w = 0; w < W; ++w) T += (S.N[w] + (1LL << gs) - 1) >> gs;
-                if (T <= TOPCAP) break;
-            }
-        }
-        S.gshift = gs;
-        int tb = 0;
-        for (int w = 0; w < W; ++w) {
-            S.tbase[w] = tb;
-            tb += (int)((S.N[w] + (1LL << gs) - 1) >> gs);
-        }
-        S.tbase[W] = tb;
-        S.T = tb;
-        s->Tmax = std::max(s->Tmax, tb);
-        o_grp[b] = off;
-        if (gs > 0) off = align256(off + sizeof(Entry) * tb);
         o_x[b] = off;
         off = align256(off + sizeof(float) * L[b]);
         o_r[b] = off;
@@ -225,10 +199,9 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
         DevSig& S = s->hs[b];
         for (int w = 0; w < W; ++w) {
             S.plane[w] = (float2*)(base + o_plane[b * W + w]);
-            S.l0[w] = (Entry*)(base + o_l0[b * W + w]);
-            S.l1[w] = (Entry*)(base + o_l1[b * W + w]);
+            S.l0[w] = (Key*)(base + o_l0[b * W + w]);
+            S.l1[w] = (Key*)(base + o_l1[b * W + w]);
         }
-        S.grp = S.gshift > 0 ? (Entry*)(base + o_grp[b]) : nullptr;
         S.x = (const float*)(base + o_x[b]);
         S.r = (float*)(base + o_r[b]);
         S.y = (float*)(base + o_y[b]);
@@ -264,16 +237,6 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
             e = cudaMemcpyAsync(s->d_frame_prefix[w], fp.data(), sizeof(long long) * (B + 1),
                                 cudaMemcpyHostToDevice, st);
         // host vectors must outlive the async copies
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    }
-    if (e == cudaSuccess) {
-        std::vector<int> gp(B + 1, 0);
-        for (int b = 0; b < B; ++b) gp[b + 1] = gp[b] + (s->hs[b].gshift > 0 ? s->hs[b].T : 0);
-        s->total_groups = gp[B];
-        e = cudaMalloc(&s->d_group_prefix, sizeof(int) * (B + 1));
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(s->d_group_prefix, gp.data(), sizeof(int) * (B + 1),
-                                cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
     if (e == cudaSuccess) e = cudaMalloc(&s->d_scalar, sizeof(double) * 4);
@@ -406,7 +369,6 @@ int analysis_pass(mp_state* s, int flagged) {
         CKR(launch_tree_build(p->dp, s->d_sigs, B, s->d_frame_prefix[w], s->total_frames[w], w, st,
                               flagged));
     }
-    CKR(launch_group_build(s->d_sigs, B, s->d_group_prefix, s->total_groups, p->W, st, flagged));
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CKR(cudaStreamIsCapturing(st, &cap));
     if (tc && cap == cudaStreamCaptureStatusNone) {

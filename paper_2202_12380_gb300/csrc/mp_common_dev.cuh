@@ -49,31 +49,26 @@ __device__ __forceinline__ unsigned long long make_key_sel(float2 v, unsigned fl
            (unsigned long long)(0xffffffffu - flat);
 }
 
-__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
-    return a > b ? a : b;
-}
-
-__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long k) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) k = umax64(k, __shfl_xor_sync(FULL, k, o));
-    return k;
-}
-
-// warp-wide max Entry (key decides); every lane returns the winner.  The
-// 64-bit key is reduced as two 32-bit redux steps (score word, then the
-// inverted index among the lanes holding the top score), which is a much
-// shorter dependent chain than a shuffle tree.
-__device__ __forceinline__ Entry warp_max_entry(Entry e) {
-    const unsigned hi = (unsigned)(e.key >> 32), lo = (unsigned)e.key;
+// warp-wide max key; every lane returns it.  The 64-bit key is reduced as
+// two 32-bit redux steps (score word, then the inverted index among the
+// lanes holding the top score).
+__device__ __forceinline__ Key warp_max_key(Key k) {
+    const unsigned hi = (unsigned)(k >> 32), lo = (unsigned)k;
     const unsigned mh = __reduce_max_sync(FULL, hi);
     const unsigned ml = __reduce_max_sync(FULL, hi == mh ? lo : 0u);
-    const unsigned ball = __ballot_sync(FULL, hi == mh && lo == ml);
-    const int src = __ffs(ball) - 1;
-    Entry r;
-    r.key = ((unsigned long long)mh << 32) | ml;
-    r.val.x = __shfl_sync(FULL, e.val.x, src);
-    r.val.y = __shfl_sync(FULL, e.val.y, src);
-    return r;
+    return ((Key)mh << 32) | ml;
+}
+
+// two warp-wide max reductions run side by side (independent chains)
+__device__ __forceinline__ void warp_max_key2(Key& a, Key& b) {
+    const unsigned ha = (unsigned)(a >> 32), la = (unsigned)a;
+    const unsigned hb = (unsigned)(b >> 32), lb = (unsigned)b;
+    const unsigned mha = __reduce_max_sync(FULL, ha);
+    const unsigned mhb = __reduce_max_sync(FULL, hb);
+    const unsigned mla = __reduce_max_sync(FULL, ha == mha ? la : 0u);
+    const unsigned mlb = __reduce_max_sync(FULL, hb == mhb ? lb : 0u);
+    a = ((Key)mha << 32) | mla;
+    b = ((Key)mhb << 32) | mlb;
 }
 
 }  // namespace mpg

@@ -4,17 +4,18 @@
 //   plane[w]  residual coefficients rho_w(m, n), float2, frame-major
 //             [N_w][Mrp_w] with Mrp_w = 32 * ceil((M_w/2 + 1) / 32); bins
 //             m >= M_w/2 + 1 are zero padding and never selected
-//   l0[w]     max-tree level 0: one Entry per (frame, 32-bin chunk)
-//   l1[w]     max-tree level 1: one Entry per frame
-//   grp       level 2 (only when frames do not fit the on-chip top level):
-//             one Entry per group of 2^gshift consecutive frames of one
-//             dictionary
-// An Entry packs the selection key and the coefficient it belongs to:
+//   l0[w]     max-tree level 0: one key per (frame, 32-bin chunk)
+//   l1[w]     max-tree level 1: one key per frame
+// The MP launch keeps the top level (one key per frame, or per group of
+// 2^gshift consecutive frames of one dictionary when the frames do not fit)
+// in shared memory.  A key packs the selection score and the coefficient's
+// flat index:
 //   key = (float bits of |rho|^2) << 32 | (0xffffffff - flat index),
 //   flat = fbase[w] + n * 2^msh_w + m   (2^msh_w >= M_w/2 + 1),
 // so an unsigned max over keys is the argmax of |rho|^2 with ties broken
 // towards the lowest (w, n, m).  |rho|^2 >= 0, so its float bits order like
-// the values.
+// the values.  The tree holds keys only: the selected coefficient itself is
+// read from its plane.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,13 +27,9 @@ namespace mpg {
 
 constexpr int MAXW = 8;          // dictionaries per plan
 constexpr int CHUNK = 32;        // bins per level-0 entry (one warp)
-constexpr int TOPCAP = 4096;     // top-level entries held in shared memory
-constexpr int LOOP_THREADS = 512;
+constexpr int TOPCAP = 16384;    // top-level keys held in shared memory per CTA
 
-struct __align__(16) Entry {
-    unsigned long long key;
-    float2 val;
-};
+using Key = unsigned long long;
 
 struct DevDict {
     int wlen, a, M, Mr, nch, Mrp;  // Mr = M/2+1 stored bins, Mrp padded to CHUNK
@@ -80,13 +77,9 @@ struct DevSig {
     long long N[MAXW];
     int Nmask[MAXW];  // N_w - 1 if N_w is a power of two, else 0
     unsigned fbase[MAXW + 1];
-    int tbase[MAXW + 1];
     float2* plane[MAXW];
-    Entry* l0[MAXW];
-    Entry* l1[MAXW];
-    Entry* grp;
-    int gshift;      // log2 of frames per top-level entry
-    int T;           // top-level entries
+    Key* l0[MAXW];
+    Key* l1[MAXW];
     mp_atom* atoms;
     double* errs;
     long long cap;
@@ -123,8 +116,6 @@ cudaError_t launch_reset_residual(DevSig* d_sigs, int nsig, cudaStream_t st);
 cudaError_t launch_tree_build(const DevPlan& P, const DevSig* d_sigs, int nsig,
                               const long long* d_frame_prefix, long long total_frames, int dict,
                               cudaStream_t st, int flagged = 0);
-cudaError_t launch_group_build(const DevSig* d_sigs, int nsig, const int* d_group_prefix,
-                               long long total_groups, int W, cudaStream_t st, int flagged = 0);
 // reset_it > 0: reset after that many selections since the last reset;
 // reset_scale > 0: reset once E < E_out reset_scale
 cudaError_t launch_mp_loop(const DevPlan& P, DevSig* d_sigs, const int* d_order, int nsig,

@@ -94,15 +94,13 @@ __device__ __forceinline__ unsigned mapa_u32(unsigned addr, int rank) {
     return r;
 }
 
-// 16-byte store into another CTA's shared memory that also completes 16
-// bytes of transaction on that CTA's mbarrier
-__device__ __forceinline__ void st_async16(unsigned raddr, const Entry& e, unsigned rbar) {
-    const unsigned k0 = (unsigned)e.key, k1 = (unsigned)(e.key >> 32);
+// 8-byte store into another CTA's shared memory that also completes 8 bytes
+// of transaction on that CTA's mbarrier
+__device__ __forceinline__ void st_async8(unsigned raddr, unsigned lo, unsigned hi, unsigned rbar) {
     asm volatile(
-        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];"
+        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b32 [%0], {%1, %2}, [%3];"
         :
-        : "r"(raddr), "r"(k0), "r"(k1), "r"(__float_as_uint(e.val.x)), "r"(__float_as_uint(e.val.y)),
-          "r"(rbar)
+        : "r"(raddr), "r"(lo), "r"(hi), "r"(rbar)
         : "memory");
 }
 
@@ -255,24 +253,6 @@ __device__ __forceinline__ void build_vjob(const DevDict* sd, const DevPair* sp,
     }
 }
 
-// two warp-wide max reductions run side by side (independent chains)
-__device__ __forceinline__ void warp_max_entry2(Entry& a, Entry& b) {
-    const unsigned ha = (unsigned)(a.key >> 32), la = (unsigned)a.key;
-    const unsigned hb = (unsigned)(b.key >> 32), lb = (unsigned)b.key;
-    const unsigned mha = __reduce_max_sync(FULL, ha);
-    const unsigned mhb = __reduce_max_sync(FULL, hb);
-    const unsigned mla = __reduce_max_sync(FULL, ha == mha ? la : 0u);
-    const unsigned mlb = __reduce_max_sync(FULL, hb == mhb ? lb : 0u);
-    const unsigned sa = __ffs(__ballot_sync(FULL, ha == mha && la == mla)) - 1;
-    const unsigned sb = __ffs(__ballot_sync(FULL, hb == mhb && lb == mlb)) - 1;
-    a.key = ((unsigned long long)mha << 32) | mla;
-    b.key = ((unsigned long long)mhb << 32) | mlb;
-    const float ax = __shfl_sync(FULL, a.val.x, sa), ay = __shfl_sync(FULL, a.val.y, sa);
-    const float bx = __shfl_sync(FULL, b.val.x, sb), by = __shfl_sync(FULL, b.val.y, sb);
-    a.val = make_float2(ax, ay);
-    b.val = make_float2(bx, by);
-}
-
 // per-term quantities of one frame: the tile column's first entry and the
 // weight c e^{i 2 pi q / M_u} (zero when the column misses the frame)
 __device__ __forceinline__ void term_frame(int act, int Acol, int C, int R, int qb, int dq,
@@ -293,8 +273,8 @@ __device__ __forceinline__ void term_frame(int act, int Acol, int C, int R, int 
 template <int NT, bool POW2>
 __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     k_mp_loop(DevPlan P, DevSig* __restrict__ sigs, const int* __restrict__ order,
-              long long kmax, double thr_scale, long long budget_ns, int CS, long long reset_it,
-              double reset_scale) {
+              long long kmax, double thr_scale, long long budget_ns, int CS, int topcap,
+              long long reset_it, double reset_scale) {
     namespace cg = cooperative_groups;
     constexpr int NWARPS = NT / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -306,11 +286,14 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     __shared__ int sstop[2];        // stop decision per iteration parity
     __shared__ int ltb[MAXW + 1];   // local top-level base per dictionary
     __shared__ int clo[MAXW + 1];   // chunk-list base per dictionary
+    __shared__ int sgs;             // log2 of frames per top-level key (single CTA)
     __shared__ int ndirty;          // dirty top-level groups this iteration
-    __shared__ Entry wsel[NWARPS];  // per-warp bests of the scan
-    __shared__ __align__(16) Entry cand[2][16];      // CTA bests of the cluster, per parity
-    __shared__ __align__(16) int tmsg[2][4];         // time-limit message of CTA 0, per parity
-    __shared__ __align__(8) unsigned long long xbar[2];  // exchange barriers, per parity
+    __shared__ Key wsel[NWARPS];    // per-warp bests of the scan
+    __shared__ __align__(8) Key cand[2][16];   // CTA bests of the cluster, per parity
+    __shared__ __align__(8) Key tmsg[2];       // time-limit message of CTA 0, per parity
+    __shared__ __align__(8) float2 cval[2];    // selected coefficient, per parity
+    __shared__ __align__(8) unsigned long long xbar[2];  // candidate barriers, per parity
+    __shared__ __align__(8) unsigned long long vbar[2];  // coefficient barriers, per parity
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = CS > 1 ? (int)cluster.block_rank() : 0;
     const int cs_sh = __ffs(CS) - 1;
@@ -326,19 +309,35 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     for (int i = tid; i < W * W; i += NT) sp[i] = P.p[i];
     const unsigned xb0 = (unsigned)__cvta_generic_to_shared(&xbar[0]);
     const unsigned xb1 = (unsigned)__cvta_generic_to_shared(&xbar[1]);
+    const unsigned vb0 = (unsigned)__cvta_generic_to_shared(&vbar[0]);
+    const unsigned vb1 = (unsigned)__cvta_generic_to_shared(&vbar[1]);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(xb0));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(xb1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(vb0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(vb1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        tmsg[0][0] = tmsg[1][0] = 0;
+        tmsg[0] = tmsg[1] = 0ull;
         ndirty = 0;
     }
     __syncthreads();
     if (tid == 0) {
+        // top level: this CTA's frames (cluster), else every frame, grouped
+        // by 2^gs so that at most topcap keys are held
+        int gs = 0;
+        if (CS == 1) {
+            for (;;) {
+                long long t = 0;
+                for (int w = 0; w < W; ++w) t += (S.N[w] + (1ll << gs) - 1) >> gs;
+                if (t <= topcap || gs >= 30) break;
+                ++gs;
+            }
+        }
+        sgs = gs;
         int b = 0, c = 0;
         for (int w = 0; w < W; ++w) {
             ltb[w] = b;
-            b += CS > 1 ? (int)(S.N[w] / CS) : S.tbase[w + 1] - S.tbase[w];
+            b += CS > 1 ? (int)(S.N[w] / CS) : (int)((S.N[w] + (1ll << gs) - 1) >> gs);
             clo[w] = c;
             c += (P.d[w].nch + 7) & ~7;
         }
@@ -347,8 +346,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     }
     __syncthreads();
     const int T = ltb[W];
-    Entry* top = reinterpret_cast<Entry*>(smem_raw);
-    DevClass* scls = reinterpret_cast<DevClass*>(top + T);
+    const int gsh = sgs;
+    Key* top = reinterpret_cast<Key*>(smem_raw);
+    DevClass* scls = reinterpret_cast<DevClass*>(top + ((T + 1) & ~1));
     float2* sgam = reinterpret_cast<float2*>(scls + P.ncls);
     float2* scis = sgam + P.ngam;
     unsigned* dbits = reinterpret_cast<unsigned*>(scis + P.ncis);  // dirty groups, one bit each
@@ -360,11 +360,18 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     for (int i = tid; i < P.ncis; i += NT) scis[i] = P.cis[i];
     for (int w = 0; w < W; ++w) {
         const int tb = ltb[w], te = ltb[w + 1];
+        const Key* l1 = S.l1[w];
         if (CS > 1) {
-            for (int i = tid; i < te - tb; i += NT) top[tb + i] = S.l1[w][(long long)i * CS + rank];
+            for (int i = tid; i < te - tb; i += NT) top[tb + i] = l1[(long long)i * CS + rank];
         } else {
-            const Entry* src = S.gshift == 0 ? S.l1[w] : S.grp + S.tbase[w];
-            for (int i = tid; i < te - tb; i += NT) top[tb + i] = src[i];
+            const long long Nw = S.N[w];
+            for (int i = tid; i < te - tb; i += NT) {
+                const long long f0 = (long long)i << gsh;
+                const long long f1 = min(f0 + (1ll << gsh), Nw);
+                Key m = 0ull;
+                for (long long f = f0; f < f1; ++f) m = l1[f] > m ? l1[f] : m;
+                top[tb + i] = m;
+            }
         }
     }
     for (int i = tid; i < ((T + 31) >> 5); i += NT) dbits[i] = 0u;
@@ -386,7 +393,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     const double E_out = S.E_out;
     const unsigned long long t_start = gtimer();
     const float2* __restrict__ tiles = P.tiles;
-    const unsigned xbytes = (unsigned)(CS * sizeof(Entry)) + (budget_ns > 0 ? 16u : 0u);
+    const unsigned xbytes = (unsigned)(CS * sizeof(Key)) + (budget_ns > 0 ? 8u : 0u);
     int stop = 0;
     if (tid == KEEPER) {
         int s0 = 0;
@@ -407,53 +414,56 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     for (;;) {
         const int par = (int)(it & 1);
         const unsigned xb = par ? xb1 : xb0;
+        const unsigned vb = par ? vb1 : vb0;
+        const unsigned xpar = (unsigned)((it >> 1) & 1);
         // ---- 1. scan of the top level, CTA best, cluster exchange ----------
         {
-            Entry b;
-            b.key = 0;
-            b.val = make_float2(0.f, 0.f);
-            for (int i = tid; i < T; i += NT) {
-                const Entry e = top[i];
-                if (e.key > b.key) b = e;
+            // four independent running maxima, merged at the end
+            Key b0 = 0ull, b1 = 0ull, b2 = 0ull, b3 = 0ull;
+            int i = tid;
+            for (; i + 3 * NT < T; i += 4 * NT) {
+                const Key e0 = top[i], e1 = top[i + NT], e2 = top[i + 2 * NT], e3 = top[i + 3 * NT];
+                b0 = e0 > b0 ? e0 : b0;
+                b1 = e1 > b1 ? e1 : b1;
+                b2 = e2 > b2 ? e2 : b2;
+                b3 = e3 > b3 ? e3 : b3;
             }
-            const Entry r = warp_max_entry(b);
+            for (; i < T; i += NT) b0 = top[i] > b0 ? top[i] : b0;
+            b0 = b1 > b0 ? b1 : b0;
+            b2 = b3 > b2 ? b3 : b2;
+            b0 = b2 > b0 ? b2 : b0;
+            const Key r = warp_max_key(b0);
             if (lane == 0) wsel[warp] = r;
-            if (CS > 1 && tid == 0)
+            if (CS > 1 && tid == 0) {
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(xb),
                              "r"(xbytes)
                              : "memory");
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(vb),
+                             "r"(8u)
+                             : "memory");
+            }
         }
         __syncthreads();
-        Entry best;
-        {
-            Entry b;
-            b.key = 0;
-            b.val = make_float2(0.f, 0.f);
-            if (lane < NWARPS) b = wsel[lane];
-            best = warp_max_entry(b);
-        }
+        Key best = warp_max_key(lane < NWARPS ? wsel[lane] : 0ull);
         if (CS > 1) {
             if (warp == 0) {
                 if (lane < CS) {
                     const unsigned laddr = (unsigned)__cvta_generic_to_shared(&cand[par][rank]);
-                    st_async16(mapa_u32(laddr, lane), best, mapa_u32(xb, lane));
+                    st_async8(mapa_u32(laddr, lane), (unsigned)best, (unsigned)(best >> 32),
+                              mapa_u32(xb, lane));
                 }
                 if (budget_ns > 0 && rank == 0) {
                     int tf = 0;
                     if (lane == 0) tf = (long long)(gtimer() - t_start) > budget_ns ? 1 : 0;
                     tf = __shfl_sync(FULL, tf, 0);
                     if (lane < CS) {
-                        Entry m;
-                        m.key = (unsigned long long)(unsigned)tf;
-                        m.val = make_float2(0.f, 0.f);
-                        const unsigned laddr = (unsigned)__cvta_generic_to_shared(&tmsg[par][0]);
-                        st_async16(mapa_u32(laddr, lane), m, mapa_u32(xb, lane));
+                        const unsigned laddr = (unsigned)__cvta_generic_to_shared(&tmsg[par]);
+                        st_async8(mapa_u32(laddr, lane), (unsigned)tf, 0u, mapa_u32(xb, lane));
                     }
                 }
             }
             // bounded wait for the CS candidates (and the time-limit message)
             const unsigned long long w0 = gtimer();
-            const unsigned xpar = (unsigned)((it >> 1) & 1);
             bool ok = true;
             while (!xbar_try(xb, xpar)) {
                 if (gtimer() - w0 > 2000000000ull) {
@@ -461,26 +471,22 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                     break;
                 }
             }
-            Entry b;
-            b.key = 0;
-            b.val = make_float2(0.f, 0.f);
-            if (lane < CS) b = cand[par][lane];
-            best = warp_max_entry(b);
+            best = warp_max_key(lane < CS ? cand[par][lane] : 0ull);
             if (!ok) stop = -2;
         } else if (budget_ns > 0) {
             // single CTA: the time limit is read by one thread before the scan
             // barrier of the next iteration; here it is read after this one
-            if (tid == 0) tmsg[par][0] = (long long)(gtimer() - t_start) > budget_ns ? 1 : 0;
+            if (tid == 0) tmsg[par] = (long long)(gtimer() - t_start) > budget_ns ? 1ull : 0ull;
             __syncthreads();
         }
 
-        // ---- 2. selection, adjustment, bookkeeping -------------------------
+        // ---- 2. selection ---------------------------------------------------
         if (stop == 0) stop = sstop[k & 1];
-        if (stop == 0 && budget_ns > 0 && tmsg[par][0]) stop = -1;
-        if (stop == 0 && (unsigned)(best.key >> 32) == 0u) stop = MP_STOP_ZEROMAX;
+        if (stop == 0 && budget_ns > 0 && tmsg[par]) stop = -1;
+        if (stop == 0 && (unsigned)(best >> 32) == 0u) stop = MP_STOP_ZEROMAX;
         if (stop) break;
 
-        const unsigned flat = 0xffffffffu - (unsigned)(best.key & 0xffffffffull);
+        const unsigned flat = 0xffffffffu - (unsigned)(best & 0xffffffffull);
         // dictionary of the flat index: the number of bases w >= 1 at or below it
         const int u = __popc(__ballot_sync(FULL, lane > 0 && lane < W && flat >= fb_l));
         const unsigned rel = flat - __shfl_sync(FULL, fb_l, u);
@@ -489,9 +495,46 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         const int kk = (int)(rel & ((1u << msh) - 1u));
         const int Mu = sd[u].M;
         const bool edge = (kk == 0) || (2 * kk == Mu);
+        // the selected coefficient: a single CTA reads it from its plane (it
+        // wrote it itself); in a cluster the CTA owning frame j reads it and
+        // sends it to every CTA of the cluster (bytes completed on vbar),
+        // while the update descriptors are built
+        float2 rho = make_float2(0.f, 0.f);
+        const float2* psel = S.plane[u] + (long long)j * sd[u].Mrp + kk;
+        if (CS == 1) {
+            rho = *psel;
+        } else if (warp == NWARPS - 1 && (j & (CS - 1)) == rank) {
+            float2 r2 = make_float2(0.f, 0.f);
+            if (lane == 0) r2 = *psel;
+            const unsigned lo = __shfl_sync(FULL, __float_as_uint(r2.x), 0);
+            const unsigned hi = __shfl_sync(FULL, __float_as_uint(r2.y), 0);
+            if (lane < CS) {
+                const unsigned laddr = (unsigned)__cvta_generic_to_shared(&cval[par]);
+                st_async8(mapa_u32(laddr, lane), lo, hi, mapa_u32(vb, lane));
+            }
+        }
+
+        // ---- 3. per-dictionary update descriptors ---------------------------
+        for (int v = warp; v < W; v += NWARPS)
+            build_vjob<POW2>(sd, sp, scls, W, S, u, kk, j, edge, v, rank, CS, cs_sh, lane, &vj[v],
+                             chl + clo[v], tmk[v]);
+        __syncthreads();
+        if (CS > 1) {
+            const unsigned long long w0 = gtimer();
+            while (!xbar_try(vb, xpar)) {
+                if (gtimer() - w0 > 2000000000ull) {
+                    stop = -2;
+                    break;
+                }
+            }
+            rho = cval[par];
+            if (stop) break;
+        }
+
+        // ---- 4. real-pair adjustment and bookkeeping ------------------------
         // eqs. dualatprod / projenfaster: coefficient and energy drop in FP32
         // (gamma is zero away from m = 0 and m = M/2), E accumulated in FP64
-        const float rx = best.val.x, ry = best.val.y;
+        const float rx = rho.x, ry = rho.y;
         float cx, cy, Edf;
         if (edge) {
             cx = rx;
@@ -534,13 +577,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         }
         ++k;
 
-        // ---- 3. per-dictionary update descriptors ---------------------------
-        for (int v = warp; v < W; v += NWARPS)
-            build_vjob<POW2>(sd, sp, scls, W, S, u, kk, j, edge, v, rank, CS, cs_sh, lane, &vj[v],
-                             chl + clo[v], tmk[v]);
-        __syncthreads();
-
-        // ---- 4. frame jobs, dealt from one flat index -----------------------
+        // ---- 5. frame jobs, dealt from one flat index -----------------------
         {
             const float2 c_main = make_float2(cx, cy), c_conj = make_float2(cx, -cy);
             const int Mumask = sd[u].Mmask;
@@ -563,18 +600,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                 int n = J.nstart + f * CS;
                 n -= (n >= Nv) ? Nv : 0;
                 n -= (n >= Nv) ? Nv : 0;
-                // level-0 entries of the whole frame (touched ones are replaced)
-                Entry* l0row = S.l0[v] + (long long)n * nch;
-                Entry l0v[MAXL0];
+                // level-0 keys of the whole frame (touched ones are recomputed)
+                Key* l0row = S.l0[v] + (long long)n * nch;
+                Key l0v[MAXL0];
 #pragma unroll
                 for (int q = 0; q < MAXL0; ++q) {
                     const int c = lane + 32 * q;
-                    if (c < nch) {
-                        l0v[q] = l0row[c];
-                    } else {
-                        l0v[q].key = 0ull;
-                        l0v[q].val = make_float2(0.f, 0.f);
-                    }
+                    l0v[q] = c < nch ? l0row[c] : 0ull;
                 }
                 float2* prow = S.plane[v] + (long long)n * Dv.Mrp;
                 float2 w0, w1;
@@ -586,17 +618,14 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                 const unsigned short* lst = chl + clo[v];
                 const unsigned fn = S.fbase[v] + ((unsigned)n << Dv.msh);
                 const unsigned tm = tmk[v][lane];
-                // maximum of the touched chunks' new level-0 entries (uniform)
-                Entry tmax;
-                tmax.key = 0ull;
-                tmax.val = make_float2(0.f, 0.f);
+                Key tmax = 0ull;  // maximum of the touched chunks' new keys
                 for (int b0 = 0; b0 < J.nlist; b0 += CB) {
                     const int nb = min(CB, J.nlist - b0);  // uniform
                     int cq[CB];
                     float2 val[CB], h0[CB], h1[CB];
                     bool hit[CB];
-#pragma unroll
-                    for (int q = 0; q < CB; ++q) {
+                    // loads of one slot: the plane chunk and both terms' tile entries
+                    auto load_slot = [&](int q) {
                         cq[q] = q < nb ? (int)lst[b0 + q] : -1;
                         const int m = cq[q] * CHUNK + lane;
                         const bool ok = cq[q] >= 0;
@@ -610,10 +639,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                         h0[q] = s0 ? __ldg(tiles + tb0 + i0) : make_float2(0.f, 0.f);
                         h1[q] = s1 ? __ldg(tiles + tb1 + i1) : make_float2(0.f, 0.f);
                         hit[q] = s0 || s1;
-                    }
-                    Entry e[CB];
-#pragma unroll
-                    for (int q = 0; q < CB; ++q) {
+                    };
+                    Key e[CB];
+                    // update and key of one slot
+                    auto update_slot = [&](int q) {
                         const int m = cq[q] * CHUNK + lane;
                         float2 x2 = val[q];
                         const float2 d0 = cmul(w0, h0[q]);
@@ -623,45 +652,58 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                         x2.x -= d1.x;
                         x2.y -= d1.y;
                         if (hit[q]) prow[m] = x2;
-                        e[q].val = x2;
-                        e[q].key = (cq[q] >= 0 && m < Mr)
-                                       ? make_key_sel(x2, fn + m, m, Dv, sgam, P.pedantic)
-                                       : 0ull;
+                        e[q] = (cq[q] >= 0 && m < Mr)
+                                   ? make_key_sel(x2, fn + m, m, Dv, sgam, P.pedantic)
+                                   : 0ull;
+                    };
+                    // all loads first (one round trip), the second pair only
+                    // when the batch holds more than two chunks
+                    load_slot(0);
+                    load_slot(1);
+                    if (nb > 2) {
+                        load_slot(2);
+                        load_slot(3);
                     }
-                    // chunk maxima, two at a time; the second pair only when
-                    // the batch holds more than two chunks
-                    warp_max_entry2(e[0], e[1]);
-                    if (nb > 2) warp_max_entry2(e[2], e[3]);
-#pragma unroll
-                    for (int q = 0; q < CB; ++q) {
-                        if (q < nb) {
-                            if (lane == q) l0row[cq[q]] = e[q];
-                            if (e[q].key > tmax.key) tmax = e[q];
+                    update_slot(0);
+                    update_slot(1);
+                    warp_max_key2(e[0], e[1]);
+                    if (lane == 0) l0row[cq[0]] = e[0];
+                    tmax = e[0] > tmax ? e[0] : tmax;
+                    if (nb > 1) {
+                        if (lane == 1) l0row[cq[1]] = e[1];
+                        tmax = e[1] > tmax ? e[1] : tmax;
+                    }
+                    if (nb > 2) {
+                        update_slot(2);
+                        update_slot(3);
+                        warp_max_key2(e[2], e[3]);
+                        if (lane == 2) l0row[cq[2]] = e[2];
+                        tmax = e[2] > tmax ? e[2] : tmax;
+                        if (nb > 3) {
+                            if (lane == 3) l0row[cq[3]] = e[3];
+                            tmax = e[3] > tmax ? e[3] : tmax;
                         }
                     }
                 }
-                // frame maximum: the touched chunks' new entries and the
-                // untouched chunks' stored ones
-                Entry fb = tmax;
+                // frame maximum: the touched chunks' new keys and the untouched
+                // chunks' stored ones
+                Key fb = tmax;
 #pragma unroll
                 for (int s = 0; s < MAXL0; ++s)
-                    if (!((tm >> s) & 1u) && l0v[s].key > fb.key) fb = l0v[s];
+                    if (!((tm >> s) & 1u) && l0v[s] > fb) fb = l0v[s];
                 if (nch > 32 * MAXL0) {
                     __syncwarp();  // this warp's level-0 stores are visible to its loads
-                    for (int c = lane + 32 * MAXL0; c < nch; c += 32) {
-                        const Entry e = l0row[c];
-                        if (e.key > fb.key) fb = e;
-                    }
+                    for (int c = lane + 32 * MAXL0; c < nch; c += 32) fb = l0row[c] > fb ? l0row[c] : fb;
                 }
-                const Entry fr = warp_max_entry(fb);
+                const Key fr = warp_max_key(fb);
                 if (lane == 0) {
                     S.l1[v][n] = fr;
                     if (CS > 1) {
                         top[ltb[v] + (n >> cs_sh)] = fr;
-                    } else if (S.gshift == 0) {
+                    } else if (gsh == 0) {
                         top[ltb[v] + n] = fr;
                     } else {
-                        const int gi = ltb[v] + (n >> S.gshift);
+                        const int gi = ltb[v] + (n >> gsh);
                         const unsigned bit = 1u << (gi & 31);
                         if (!(atomicOr(&dbits[gi >> 5], bit) & bit))
                             dlist[atomicAdd(&ndirty, 1)] = (unsigned short)gi;
@@ -671,22 +713,25 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         }
         __syncthreads();
 
-        // ---- 5. level 2 (groups) of touched frames (single-CTA launches) ----
-        if (CS == 1 && S.gshift > 0) {
+        // ---- 6. groups of touched frames (single CTA, grouped top level) ----
+        if (CS == 1 && gsh > 0) {
             const int nd = ndirty;
             for (int i = tid; i < nd; i += NT) {
                 const int gi = dlist[i];
                 int w = 0;
-                while (w + 1 < W && S.tbase[w + 1] <= gi) ++w;
-                const int f0 = (gi - S.tbase[w]) << S.gshift;
-                const int f1 = min(f0 + (1 << S.gshift), (int)S.N[w]);
-                const Entry* l1 = S.l1[w];
-                Entry m2 = l1[f0];
-                for (int f = f0 + 1; f < f1; ++f) {
-                    const Entry e = l1[f];
-                    if (e.key > m2.key) m2 = e;
+                while (w + 1 < W && ltb[w + 1] <= gi) ++w;
+                const int f0 = (gi - ltb[w]) << gsh;
+                const int f1 = min(f0 + (1 << gsh), (int)S.N[w]);
+                const Key* l1 = S.l1[w];
+                Key m2 = 0ull;
+                // the group's level-1 keys, eight independent loads at a time
+                for (int f = f0; f < f1; f += 8) {
+                    Key e8[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) e8[q] = f + q < f1 ? l1[f + q] : 0ull;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) m2 = e8[q] > m2 ? e8[q] : m2;
                 }
-                S.grp[gi] = m2;
                 top[gi] = m2;
                 dbits[gi >> 5] = 0u;
             }
@@ -715,7 +760,25 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
 }
 
 using LoopKernel = void (*)(DevPlan, DevSig*, const int*, long long, double, long long, int,
-                           long long, double);
+                           int, long long, double);
+
+// top-level keys a single CTA may hold: 512-thread CTAs run one per SM,
+// 256-thread CTAs two and 128-thread CTAs three, so the shared memory of the
+// top level shrinks with the CTA
+int loop_topcap(int threads) { return threads >= 512 ? TOPCAP : threads == 256 ? TOPCAP / 2 : TOPCAP / 4; }
+
+// top-level keys of a signal run by a single CTA: every frame, or groups of
+// 2^gs frames with the smallest gs that fits the cap (the kernel makes the
+// same choice)
+int single_top(const DevSig& S, int W, int cap) {
+    long long t = 0;
+    for (int gs = 0;; ++gs) {
+        t = 0;
+        for (int w = 0; w < W; ++w) t += (S.N[w] + (1ll << gs) - 1) >> gs;
+        if (t <= cap || gs >= 30) break;
+    }
+    return (int)t;
+}
 
 // the loop instantiation for a CTA size (0 if unsupported)
 LoopKernel loop_kernel(int threads, bool pow2) {
@@ -772,7 +835,7 @@ int max_clusters(LoopKernel kf, int threads, int cs, size_t smem) {
 size_t mp_loop_smem_bytes(const DevPlan& P, int T, int, int) {
     size_t chl = 0;
     for (int w = 0; w < P.W; ++w) chl += (size_t)((P.d[w].nch + 7) & ~7);
-    size_t b = (size_t)T * sizeof(Entry) + (size_t)P.ncls * sizeof(DevClass) +
+    size_t b = (size_t)((T + 1) & ~1) * sizeof(Key) + (size_t)P.ncls * sizeof(DevClass) +
                (size_t)(P.ngam + P.ncis) * sizeof(float2) + 4 * (size_t)((T + 31) >> 5) +
                2 * (size_t)((T + 7) & ~7) + 2 * chl;
     return (b + 15) & ~(size_t)15;
@@ -795,7 +858,10 @@ bool mp_loop_shape_ok(const DevPlan& P, const DevSig* hs, int B, int threads, in
     if (c != 1 && c != 2 && c != 4 && c != 8 && c != 16) return false;
     if (c == 1) {
         int tmax = 1;
-        for (int b = 0; b < B; ++b) tmax = hs[b].T > tmax ? hs[b].T : tmax;
+        for (int b = 0; b < B; ++b) {
+            const int t = single_top(hs[b], P.W, loop_topcap(threads));
+            tmax = t > tmax ? t : tmax;
+        }
         *smem = mp_loop_smem_bytes(P, tmax, threads, 1);
         return *smem <= 227 * 1024;
     }
@@ -853,9 +919,13 @@ void mp_loop_shape(const DevPlan& P, const DevSig* hs, int B, int num_sms, int* 
         *smem = sm;
         return;
     }
+    nt = nt_override ? nt_override : mp_loop_threads(B, num_sms);
     int tmax = 1;
-    for (int b = 0; b < B; ++b) tmax = hs[b].T > tmax ? hs[b].T : tmax;
-    *threads = nt_override ? nt_override : mp_loop_threads(B, num_sms);
+    for (int b = 0; b < B; ++b) {
+        const int t = single_top(hs[b], P.W, loop_topcap(nt));
+        tmax = t > tmax ? t : tmax;
+    }
+    *threads = nt;
     *cs = 1;
     *smem = mp_loop_smem_bytes(P, tmax, nt, 1);
 }
@@ -871,8 +941,8 @@ cudaError_t launch_mp_loop(const DevPlan& P, DevSig* d_sigs, const int* d_order,
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = loop_config(nsig, threads, cs, smem, st, attr);
-    e = cudaLaunchKernelEx(&cfg, kf, P, d_sigs, d_order, kmax, thr_scale, budget_ns, cs, reset_it,
-                           reset_scale);
+    e = cudaLaunchKernelEx(&cfg, kf, P, d_sigs, d_order, kmax, thr_scale, budget_ns, cs,
+                           loop_topcap(threads), reset_it, reset_scale);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -47,12 +47,11 @@ struct StaticTables {
     DevSig sig;
     long long tile_prefix[MAXW][2];
     long long frame_prefix[MAXW][2];
-    int group_prefix[2];
 };
 
 struct StaticLayout {
-    size_t o_sig, o_order, o_tp, o_fp, o_gp, o_errs, total;
-    size_t o_plane[MAXW], o_l0[MAXW], o_l1[MAXW], o_grp, o_x;
+    size_t o_sig, o_order, o_tp, o_fp, o_errs, total;
+    size_t o_plane[MAXW], o_l0[MAXW], o_l1[MAXW], o_x;
 };
 
 size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -69,9 +68,6 @@ __global__ void k_static_init(StaticTables t, unsigned char* base, StaticLayout 
         fp[2 * w] = t.frame_prefix[w][0];
         fp[2 * w + 1] = t.frame_prefix[w][1];
     }
-    int* gp = reinterpret_cast<int*>(base + lay.o_gp);
-    gp[0] = t.group_prefix[0];
-    gp[1] = t.group_prefix[1];
 }
 
 // device address of the scratch array for the current device; the first
@@ -141,23 +137,19 @@ extern "C" int mp_decompose_static(const mp_plan* p, const float* x_dev, int64_t
     off = al(off + sizeof(long long) * 2 * MAXW);
     lay.o_fp = off;
     off = al(off + sizeof(long long) * 2 * MAXW);
-    lay.o_gp = off;
-    off = al(off + sizeof(int) * 2);
     unsigned long long P = 0;
-    long long F = 0;
     for (int w = 0; w < W; ++w) {
         const DevDict& D = p->dp.d[w];
         S.N[w] = L / D.a;
         S.Nmask[w] = (S.N[w] & (S.N[w] - 1)) == 0 ? (int)(S.N[w] - 1) : 0;
         S.fbase[w] = (unsigned)P;
         P += (unsigned long long)S.N[w] << D.msh;
-        F += S.N[w];
         lay.o_plane[w] = off;
         off = al(off + sizeof(float2) * S.N[w] * D.Mrp);
         lay.o_l0[w] = off;
-        off = al(off + sizeof(Entry) * S.N[w] * D.nch);
+        off = al(off + sizeof(Key) * S.N[w] * D.nch);
         lay.o_l1[w] = off;
-        off = al(off + sizeof(Entry) * S.N[w]);
+        off = al(off + sizeof(Key) * S.N[w]);
         t.tile_prefix[w][1] = (S.N[w] + 63) / 64;
         t.frame_prefix[w][1] = S.N[w];
     }
@@ -166,24 +158,6 @@ extern "C" int mp_decompose_static(const mp_plan* p, const float* x_dev, int64_t
         return MP_EINVAL;
     }
     S.fbase[W] = (unsigned)P;
-    int gs = 0;
-    if (F > TOPCAP)
-        for (gs = 1; gs < 40; ++gs) {
-            long long T = 0;
-            for (int w = 0; w < W; ++w) T += (S.N[w] + (1LL << gs) - 1) >> gs;
-            if (T <= TOPCAP) break;
-        }
-    S.gshift = gs;
-    int tb = 0;
-    for (int w = 0; w < W; ++w) {
-        S.tbase[w] = tb;
-        tb += (int)((S.N[w] + (1LL << gs) - 1) >> gs);
-    }
-    S.tbase[W] = tb;
-    S.T = tb;
-    t.group_prefix[1] = gs > 0 ? tb : 0;
-    lay.o_grp = off;
-    if (gs > 0) off = al(off + sizeof(Entry) * tb);
     lay.o_x = off;
     off = al(off + sizeof(float) * L);
     lay.o_errs = off;
@@ -200,10 +174,9 @@ extern "C" int mp_decompose_static(const mp_plan* p, const float* x_dev, int64_t
     if (rc) return rc;
     for (int w = 0; w < W; ++w) {
         S.plane[w] = reinterpret_cast<float2*>(base + lay.o_plane[w]);
-        S.l0[w] = reinterpret_cast<Entry*>(base + lay.o_l0[w]);
-        S.l1[w] = reinterpret_cast<Entry*>(base + lay.o_l1[w]);
+        S.l0[w] = reinterpret_cast<Key*>(base + lay.o_l0[w]);
+        S.l1[w] = reinterpret_cast<Key*>(base + lay.o_l1[w]);
     }
-    S.grp = gs > 0 ? reinterpret_cast<Entry*>(base + lay.o_grp) : nullptr;
     S.x = reinterpret_cast<const float*>(base + lay.o_x);
     S.atoms = atoms_dev;
     S.errs = errors_dev ? errors_dev : reinterpret_cast<double*>(base + lay.o_errs);
@@ -214,7 +187,6 @@ extern "C" int mp_decompose_static(const mp_plan* p, const float* x_dev, int64_t
     const int* d_order = reinterpret_cast<const int*>(base + lay.o_order);
     const long long* d_tp = reinterpret_cast<const long long*>(base + lay.o_tp);
     const long long* d_fp = reinterpret_cast<const long long*>(base + lay.o_fp);
-    const int* d_gp = reinterpret_cast<const int*>(base + lay.o_gp);
     cudaError_t e;
 #define CKS(call)                                                                        \
     do {                                                                                 \
@@ -234,7 +206,6 @@ extern "C" int mp_decompose_static(const mp_plan* p, const float* x_dev, int64_t
                                   d_tp + 2 * w, d_sig, w, t.tile_prefix[w][1], st));
         CKS(launch_tree_build(p->dp, d_sig, 1, d_fp + 2 * w, t.frame_prefix[w][1], w, st));
     }
-    CKS(launch_group_build(d_sig, 1, d_gp, t.group_prefix[1], W, st));
     const double thr_scale = std::pow(10.0, -target_snr_db / 10.0);
     int threads = 0, cs = 1;
     size_t smem = 0;
