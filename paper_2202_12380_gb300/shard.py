@@ -1,0 +1,41 @@
+"""Multi-GPU helpers.
+
+A batch of signals shards across ranks with no exchange on the data path:
+every signal is decomposed by exactly one rank (the pursuit of one signal
+never reads another's coefficients), so the only collective is the
+reduction of the totals (atoms selected, slowest rank's time).  One signal
+does not shard -- each iteration needs the global argmax of the previous
+update -- so a single-signal run on N GPUs is N replicas.
+"""
+from __future__ import annotations
+
+
+def partition(lengths, nranks: int):
+    """Length-balanced assignment of signals to ranks (longest first to the
+    least-loaded rank, ties to the lower rank).  Returns one ascending list
+    of signal indices per rank; deterministic for given inputs."""
+    if nranks < 1:
+        raise ValueError("nranks must be >= 1")
+    order = sorted(range(len(lengths)), key=lambda i: (-int(lengths[i]), i))
+    load = [0] * nranks
+    out = [[] for _ in range(nranks)]
+    for i in order:
+        r = min(range(nranks), key=lambda q: (load[q], q))
+        out[r].append(i)
+        load[r] += int(lengths[i])
+    return [sorted(s) for s in out]
+
+
+def reduce_totals(seconds: float, atoms: float, device="cpu"):
+    """(max seconds over ranks, sum of atoms over ranks) through
+    torch.distributed; the identity without an initialised process group."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(seconds), float(atoms)
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    a = torch.tensor([float(atoms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(a, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(a.item())
