@@ -366,7 +366,10 @@ def run_batched(args, mg, torch, ws=1, rank=0):
     plan = mg.mp_plan_create([d[0] for d in dicts], [d[1] for d in dicts], [d[2] for d in dicts],
                              cfg["eps"], aflag, stream)
     xd = [torch.from_numpy(x).cuda() for x in xs]
-    shape, tune_ms = autotune.tune(plan, xd, k_probe=args.tune_atoms, stream=stream)
+    # probe: the workload itself (its K and stop target), so the tail of the
+    # long signals is part of what the tuner compares
+    shape, tune_ms = autotune.tune(plan, xd, k_probe=args.tune_atoms or cfg["kmax"],
+                                   target_snr_db=cfg["snr_db"], stream=stream, repeats=1)
     state = mg.mp_analyze(plan, xd)
     mg.mp_state_set_launch(state, *shape)
     mg.mp_run(state, cfg["kmax"], cfg["snr_db"])  # sizes the atom buffers before capture
@@ -485,8 +488,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--batched-steps", type=int, default=3)
-    ap.add_argument("--tune-atoms", type=int, default=1500,
-                    help="atoms per launch-shape probe of the batched autotuner")
+    ap.add_argument("--tune-atoms", type=int, default=0,
+                    help="atoms per launch-shape probe of the batched autotuner "
+                         "(0: the workload's K)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-atoms", type=int, default=50000)
     ap.add_argument("--ref-atoms", type=int, default=10000)

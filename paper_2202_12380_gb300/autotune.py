@@ -2,10 +2,13 @@
 
 The shape of the persistent MP launch -- threads per CTA and CTAs per signal
 (thread-block cluster size) -- does not change the result, only the speed.
-``tune`` times every feasible shape on a short probe of the caller's own
-workload (the first ``k_probe`` atoms), picks the fastest and optionally
-caches the choice in a JSON file keyed by the dictionary set and the signal
-lengths.  Apply it with ``mpgabor.mp_state_set_launch``.
+``tune`` times every feasible shape on the caller's own workload (up to
+``k_probe`` atoms per signal with the caller's stop target), picks the
+fastest and optionally caches the choice in a JSON file keyed by the
+dictionary set and the signal lengths.  Apply it with
+``mpgabor.mp_state_set_launch``.  With several signals the stop target
+matters: shapes that need two waves of CTAs win or lose by how the signals'
+pursuits end, so the probe should stop the way the real run does.
 """
 from __future__ import annotations
 

@@ -41,8 +41,7 @@ struct mp_state {
     long long total_tiles[MAXW];
     long long* d_frame_prefix[MAXW];
     long long total_frames[MAXW];
-    size_t smem;             // MP launch shape (see mp_loop_shape)
-    int threads, cs;
+    LoopShape shape;         // MP launch shape (see mp_loop_shape)
     long long cap;           // atom capacity per signal
     mp_atom* d_atoms;
     double* d_errs;
@@ -297,7 +296,13 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
         state_free(s);
         return cuda_fail(e, "mp_analyze: state set-up");
     }
-    mp_loop_shape(p->dp, s->hs.data(), B, p->num_sms, &s->threads, &s->cs, &s->smem);
+    mp_loop_shape(p->dp, s->hs.data(), B, p->num_sms, &s->shape);
+    if (s->shape.threads == 0) {
+        state_free(s);
+        mpg_set_error("mp_analyze: no MP launch shape fits these signals and dictionaries in "
+                      "shared memory");
+        return MP_ENOTCOMPAT;
+    }
     *out = s;
     return MP_OK;
 }
@@ -494,8 +499,8 @@ extern "C" int mp_run_async(mp_state* s, int64_t K_max, double target_snr_db) {
     const long long budget =
         s->time_limit_s > 0 ? (long long)std::min(s->time_limit_s * 1e9, 9e18) : 0LL;
     const double reset_scale = s->reset_db < 0.0 ? std::pow(10.0, s->reset_db / 10.0) : 0.0;
-    CKR(launch_mp_loop(s->plan->dp, s->d_sigs, s->d_order, s->B, K_max, thr_scale, budget, s->smem,
-                       s->threads, s->cs, s->plan->stream, s->reset_it, reset_scale));
+    CKR(launch_mp_loop(s->plan->dp, s->d_sigs, s->d_order, s->B, K_max, thr_scale, budget,
+                       s->shape, s->plan->stream, s->reset_it, reset_scale));
     return MP_OK;
 }
 
@@ -558,19 +563,18 @@ extern "C" int mp_state_set_launch(mp_state* s, int threads, int cluster) {
         return MP_EINVAL;
     }
     if (threads == 0 && cluster == 0) {
-        mp_loop_shape(s->plan->dp, s->hs.data(), s->B, s->plan->num_sms, &s->threads, &s->cs,
-                      &s->smem);
+        LoopShape sh;
+        mp_loop_shape(s->plan->dp, s->hs.data(), s->B, s->plan->num_sms, &sh);
+        if (sh.threads) s->shape = sh;
         return MP_OK;
     }
-    size_t smem = 0;
-    if (!mp_loop_shape_ok(s->plan->dp, s->hs.data(), s->B, threads, cluster, &smem)) {
+    LoopShape sh;
+    if (!mp_loop_shape_ok(s->plan->dp, s->hs.data(), s->B, threads, cluster, &sh)) {
         mpg_set_error("mp_state_set_launch: %d threads x cluster %d is not feasible for this "
                       "state", threads, cluster);
         return MP_EINVAL;
     }
-    s->threads = threads;
-    s->cs = cluster;
-    s->smem = smem;
+    s->shape = sh;
     return MP_OK;
 }
 
@@ -579,8 +583,8 @@ extern "C" int mp_state_get_launch(const mp_state* s, int* threads, int* cluster
         mpg_set_error("mp_state_get_launch: null state");
         return MP_EINVAL;
     }
-    if (threads) *threads = s->threads;
-    if (cluster) *cluster = s->cs;
+    if (threads) *threads = s->shape.threads;
+    if (cluster) *cluster = s->shape.cs;
     return MP_OK;
 }
 

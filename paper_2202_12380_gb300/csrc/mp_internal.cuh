@@ -37,7 +37,11 @@ struct DevDict {
     int g_off;                     // offset of the FP32 window in DevPlan::g32
     int msh;                       // flat-index row stride 2^msh >= Mr
     int Mmask;                     // M - 1 if M is a power of two, else 0
-    int cis_off;                   // offset of e^{i 2 pi q / M}, q < M, in DevPlan::cis
+    int cis_off;                   // offset of the modulation table in DevPlan::cis
+    int cis_q;                     // M/4 if 4 divides M (the table holds e^{i 2 pi q / M},
+                                   // q < M/4; quadrants are exact multiples by i), else 0
+                                   // (the table holds all q < M)
+    int cis_qsh;                   // log2(M/4) if M/4 is a power of two, else -1
 };
 
 struct DevPair {
@@ -116,15 +120,24 @@ cudaError_t launch_reset_residual(DevSig* d_sigs, int nsig, cudaStream_t st);
 cudaError_t launch_tree_build(const DevPlan& P, const DevSig* d_sigs, int nsig,
                               const long long* d_frame_prefix, long long total_frames, int dict,
                               cudaStream_t st, int flagged = 0);
+// launch shape of the MP loop: threads per CTA, CTAs per signal (cluster),
+// top-level keys a single CTA may hold (the loop groups frames to fit), and
+// the dynamic shared memory; threads = 0 means no shape fits
+struct LoopShape {
+    int threads = 0;
+    int cs = 1;
+    int topcap = 0;
+    size_t smem = 0;
+};
 // reset_it > 0: reset after that many selections since the last reset;
 // reset_scale > 0: reset once E < E_out reset_scale
 cudaError_t launch_mp_loop(const DevPlan& P, DevSig* d_sigs, const int* d_order, int nsig,
-                           long long kmax, double thr_scale, long long budget_ns, size_t smem,
-                           int threads, int cs, cudaStream_t st, long long reset_it = 0,
+                           long long kmax, double thr_scale, long long budget_ns,
+                           const LoopShape& shape, cudaStream_t st, long long reset_it = 0,
                            double reset_scale = 0.0);
-void mp_loop_shape(const DevPlan& P, const DevSig* hs, int B, int num_sms, int* threads, int* cs,
-                   size_t* smem);
-bool mp_loop_shape_ok(const DevPlan& P, const DevSig* hs, int B, int threads, int c, size_t* smem);
+void mp_loop_shape(const DevPlan& P, const DevSig* hs, int B, int num_sms, LoopShape* out);
+bool mp_loop_shape_ok(const DevPlan& P, const DevSig* hs, int B, int threads, int c,
+                      LoopShape* out);
 cudaError_t launch_synth(const DevPlan& P, const DevSig* d_sig, long long natoms, float* y,
                          long long L, cudaStream_t st);
 cudaError_t launch_resid_energy(const DevSig* d_sig, const float* y, long long L,

@@ -253,19 +253,37 @@ __device__ __forceinline__ void build_vjob(const DevDict* sd, const DevPair* sp,
     }
 }
 
+// e^{i 2 pi q / M}, q < M, from the table of dictionary D: a quarter period
+// (the quadrant k of q multiplies by i^k, exactly) or the full period
+__device__ __forceinline__ float2 cis_at(const float2* t, const DevDict& D, int q) {
+    if (D.cis_q == 0) return t[q];
+    int k, r;
+    if (D.cis_qsh >= 0) {
+        k = q >> D.cis_qsh;
+        r = q & (D.cis_q - 1);
+    } else {
+        k = q / D.cis_q;
+        r = q - k * D.cis_q;
+    }
+    const float2 e = t[r];
+    const float x = (k & 1) ? -e.y : e.x;
+    const float y = (k & 1) ? e.x : e.y;
+    return (k & 2) ? make_float2(-x, -y) : make_float2(x, y);
+}
+
 // per-term quantities of one frame: the tile column's first entry and the
 // weight c e^{i 2 pi q / M_u} (zero when the column misses the frame)
 __device__ __forceinline__ void term_frame(int act, int Acol, int C, int R, int qb, int dq,
-                                           long long tile, int n, int Nv, int Mu, int Mumask,
+                                           long long tile, int n, int Nv, const DevDict& Du,
                                            const float2* cis_u, float2 c, float2& w,
                                            long long& tbase) {
     int cc = n - Acol;
     cc += cc < 0 ? Nv : 0;
     const bool hit = act && cc < C;
     int q;
-    if (Mumask) q = (int)(((unsigned)qb + (unsigned)cc * (unsigned)dq) & (unsigned)Mumask);
-    else q = (int)(((long long)qb + (long long)cc * dq) % Mu);
-    w = hit ? cmul(c, cis_u[hit ? q : 0]) : make_float2(0.f, 0.f);
+    if (Du.Mmask) q = (int)(((unsigned)qb + (unsigned)cc * (unsigned)dq) & (unsigned)Du.Mmask);
+    else q = (int)(((long long)qb + (long long)cc * dq) % Du.M);
+    w = hit ? cmul(c, cis_at(cis_u, Du, hit ? q : 0)) : make_float2(0.f, 0.f);
     tbase = tile + (long long)cc * R;
     if (!hit) tbase = -1;
 }
@@ -580,7 +598,6 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         // ---- 5. frame jobs, dealt from one flat index -----------------------
         {
             const float2 c_main = make_float2(cx, cy), c_conj = make_float2(cx, -cy);
-            const int Mumask = sd[u].Mmask;
             const float2* cis_u = scis + sd[u].cis_off;
             // inclusive prefix of the job counts, lane w holding dictionary w's
             int pre = lane < W ? vj[lane].cnt : 0;
@@ -611,10 +628,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                 float2* prow = S.plane[v] + (long long)n * Dv.Mrp;
                 float2 w0, w1;
                 long long tb0, tb1;
-                term_frame(J.act0, J.Acol0, J.C0, J.R0, J.qb0, J.dq0, J.tile0, n, Nv, Mu, Mumask,
-                           cis_u, c_main, w0, tb0);
-                term_frame(J.act1, J.Acol1, J.C1, J.R1, J.qb1, J.dq1, J.tile1, n, Nv, Mu, Mumask,
-                           cis_u, c_conj, w1, tb1);
+                term_frame(J.act0, J.Acol0, J.C0, J.R0, J.qb0, J.dq0, J.tile0, n, Nv, sd[u], cis_u,
+                           c_main, w0, tb0);
+                term_frame(J.act1, J.Acol1, J.C1, J.R1, J.qb1, J.dq1, J.tile1, n, Nv, sd[u], cis_u,
+                           c_conj, w1, tb1);
                 const unsigned short* lst = chl + clo[v];
                 const unsigned fn = S.fbase[v] + ((unsigned)n << Dv.msh);
                 const unsigned tm = tmk[v][lane];
@@ -852,18 +869,33 @@ int mp_loop_threads(int nsig, int num_sms) {
     return nsig <= num_sms ? 512 : 256;
 }
 
-// feasibility of a requested launch shape (threads per CTA, cluster size)
-bool mp_loop_shape_ok(const DevPlan& P, const DevSig* hs, int B, int threads, int c, size_t* smem) {
+// largest dynamic shared memory of one CTA on this part
+constexpr size_t SMEM_MAX = 227 * 1024;
+
+// feasibility of a requested launch shape (threads per CTA, cluster size).
+// A single CTA per signal groups its frames so that the top level fits: the
+// cap starts at loop_topcap(threads) and halves while the shared memory
+// does not fit.  A cluster CTA holds its own frames ungrouped.
+bool mp_loop_shape_ok(const DevPlan& P, const DevSig* hs, int B, int threads, int c,
+                      LoopShape* out) {
     if (threads != 128 && threads != 256 && threads != 512) return false;
     if (c != 1 && c != 2 && c != 4 && c != 8 && c != 16) return false;
     if (c == 1) {
-        int tmax = 1;
-        for (int b = 0; b < B; ++b) {
-            const int t = single_top(hs[b], P.W, loop_topcap(threads));
-            tmax = t > tmax ? t : tmax;
+        for (int cap = loop_topcap(threads); cap >= 64; cap >>= 1) {
+            int tmax = 1;
+            for (int b = 0; b < B; ++b) {
+                const int t = single_top(hs[b], P.W, cap);
+                tmax = t > tmax ? t : tmax;
+            }
+            const size_t sm = mp_loop_smem_bytes(P, tmax, threads, 1);
+            if (sm > SMEM_MAX || mp_loop_max_clusters(threads, 1, sm) < 1) continue;
+            out->threads = threads;
+            out->cs = 1;
+            out->topcap = cap;
+            out->smem = sm;
+            return true;
         }
-        *smem = mp_loop_smem_bytes(P, tmax, threads, 1);
-        return *smem <= 227 * 1024;
+        return false;
     }
     int lt = 0;
     for (int b = 0; b < B; ++b) {
@@ -875,16 +907,19 @@ bool mp_loop_shape_ok(const DevPlan& P, const DevSig* hs, int B, int threads, in
         lt = t > lt ? t : lt;
     }
     if (lt > TOPCAP) return false;
-    *smem = mp_loop_smem_bytes(P, lt, threads, c);
-    return mp_loop_max_clusters(threads, c, *smem) >= 1;
+    const size_t sm = mp_loop_smem_bytes(P, lt, threads, c);
+    if (sm > SMEM_MAX || mp_loop_max_clusters(threads, c, sm) < 1) return false;
+    out->threads = threads;
+    out->cs = c;
+    out->topcap = TOPCAP;
+    out->smem = sm;
+    return true;
 }
 
-// launch shape for B signals: threads per CTA, cluster size and dynamic
-// shared memory.  Clusters give a signal several SMs while there are SMs to
-// spare; they need every N_w divisible by the cluster size and the per-CTA
-// top level to fit on chip.
-void mp_loop_shape(const DevPlan& P, const DevSig* hs, int B, int num_sms, int* threads, int* cs,
-                   size_t* smem) {
+// launch shape for B signals.  Clusters give a signal several SMs while there
+// are SMs to spare; they need every N_w divisible by the cluster size and the
+// per-CTA top level to fit on chip.  Otherwise one CTA per signal.
+void mp_loop_shape(const DevPlan& P, const DevSig* hs, int B, int num_sms, LoopShape* out) {
     int nt = mp_loop_threads(B, num_sms);
     int c = B <= 8 ? 16 : B <= 16 ? 8 : B * 4 <= num_sms ? 4 : B * 2 <= num_sms ? 2 : 1;
     int nt_override = 0;
@@ -896,53 +931,30 @@ void mp_loop_shape(const DevPlan& P, const DevSig* hs, int B, int num_sms, int* 
         int t = atoi(ov);
         if (t == 1 || t == 2 || t == 4 || t == 8 || t == 16) c = t;
     }
-    if (nt_override) nt = nt_override;
-    for (; c > 1; c >>= 1) {
-        // a cluster CTA runs only a few frame jobs per iteration: one warp per
-        // scheduler keeps the redundant selection off each other's issue slots
-        if (!nt_override) nt = 128;
-        bool ok = true;
-        int lt = 0;
-        for (int b = 0; b < B && ok; ++b) {
-            int t = 0;
-            for (int w = 0; w < P.W; ++w) {
-                if (hs[b].N[w] % c) ok = false;
-                t += (int)(hs[b].N[w] / c);
-            }
-            lt = t > lt ? t : lt;
-        }
-        if (!ok || lt > TOPCAP) continue;
-        const size_t sm = mp_loop_smem_bytes(P, lt, nt, c);
-        if (mp_loop_max_clusters(nt, c, sm) < 1) continue;
-        *threads = nt;
-        *cs = c;
-        *smem = sm;
-        return;
-    }
-    nt = nt_override ? nt_override : mp_loop_threads(B, num_sms);
-    int tmax = 1;
-    for (int b = 0; b < B; ++b) {
-        const int t = single_top(hs[b], P.W, loop_topcap(nt));
-        tmax = t > tmax ? t : tmax;
-    }
-    *threads = nt;
-    *cs = 1;
-    *smem = mp_loop_smem_bytes(P, tmax, nt, 1);
+    *out = LoopShape();
+    // a cluster CTA runs only a few frame jobs per iteration: one warp per
+    // scheduler keeps the redundant selection off each other's issue slots
+    for (; c > 1; c >>= 1)
+        if (mp_loop_shape_ok(P, hs, B, nt_override ? nt_override : 128, c, out)) return;
+    if (mp_loop_shape_ok(P, hs, B, nt_override ? nt_override : nt, 1, out)) return;
+    for (int t : {512, 256, 128})
+        if (mp_loop_shape_ok(P, hs, B, t, 1, out)) return;
+    *out = LoopShape();
 }
 
 cudaError_t launch_mp_loop(const DevPlan& P, DevSig* d_sigs, const int* d_order, int nsig,
-                           long long kmax, double thr_scale, long long budget_ns, size_t smem,
-                           int threads, int cs, cudaStream_t st, long long reset_it,
+                           long long kmax, double thr_scale, long long budget_ns,
+                           const LoopShape& sh, cudaStream_t st, long long reset_it,
                            double reset_scale) {
     if (nsig <= 0) return cudaSuccess;
-    LoopKernel kf = loop_kernel(threads, P.pow2 != 0);
-    if (!kf) return cudaErrorInvalidValue;
-    cudaError_t e = prepare(kf, cs, smem);
+    LoopKernel kf = loop_kernel(sh.threads, P.pow2 != 0);
+    if (!kf || sh.topcap < 1) return cudaErrorInvalidValue;
+    cudaError_t e = prepare(kf, sh.cs, sh.smem);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = loop_config(nsig, threads, cs, smem, st, attr);
-    e = cudaLaunchKernelEx(&cfg, kf, P, d_sigs, d_order, kmax, thr_scale, budget_ns, cs,
-                           loop_topcap(threads), reset_it, reset_scale);
+    cudaLaunchConfig_t cfg = loop_config(nsig, sh.threads, sh.cs, sh.smem, st, attr);
+    e = cudaLaunchKernelEx(&cfg, kf, P, d_sigs, d_order, kmax, thr_scale, budget_ns, sh.cs,
+                           sh.topcap, reset_it, reset_scale);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

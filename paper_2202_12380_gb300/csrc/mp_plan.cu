@@ -46,11 +46,11 @@ __global__ void k_cis_table(double2* cs, int M) {
     cs[q] = make_double2(c, -s);
 }
 
-// e^{+i 2 pi q / M} rounded to FP32 (modulation of eq. hkj, looked up at
-// update time)
-__global__ void k_cis32(float2* cs, int M) {
+// e^{+i 2 pi q / M} rounded to FP32 for q < n (modulation of eq. hkj,
+// looked up at update time)
+__global__ void k_cis32(float2* cs, int n, int M) {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= M) return;
+    if (q >= n) return;
     double s, c;
     sincospi(2.0 * (double)q / (double)M, &s, &c);
     cs[q] = make_float2((float)c, (float)s);
@@ -340,13 +340,19 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
         {
             int tot = 0;
             for (int w = 0; w < W; ++w) {
-                p->dp.d[w].cis_off = tot;
-                tot += M[w];
+                DevDict& D = p->dp.d[w];
+                D.cis_off = tot;
+                D.cis_q = (M[w] % 4 == 0) ? M[w] / 4 : 0;
+                D.cis_qsh = -1;
+                for (int b = 0; b < 31; ++b)
+                    if (D.cis_q == (1 << b)) D.cis_qsh = b;
+                tot += D.cis_q ? D.cis_q : M[w];
             }
             p->dp.ncis = tot;
             CK(cudaMalloc(&p->d_cis32, sizeof(float2) * tot));
             for (int w = 0; w < W; ++w) {
-                k_cis32<<<(M[w] + 255) / 256, 256, 0, st>>>(p->d_cis32 + p->dp.d[w].cis_off, M[w]);
+                const int n = p->dp.d[w].cis_q ? p->dp.d[w].cis_q : M[w];
+                k_cis32<<<(n + 255) / 256, 256, 0, st>>>(p->d_cis32 + p->dp.d[w].cis_off, n, M[w]);
                 CK(cudaGetLastError());
             }
         }

@@ -207,10 +207,13 @@ extern "C" int mp_decompose_static(const mp_plan* p, const float* x_dev, int64_t
         CKS(launch_tree_build(p->dp, d_sig, 1, d_fp + 2 * w, t.frame_prefix[w][1], w, st));
     }
     const double thr_scale = std::pow(10.0, -target_snr_db / 10.0);
-    int threads = 0, cs = 1;
-    size_t smem = 0;
-    mp_loop_shape(p->dp, &S, 1, p->num_sms, &threads, &cs, &smem);
-    CKS(launch_mp_loop(p->dp, d_sig, d_order, 1, K_max, thr_scale, 0, smem, threads, cs, st));
+    LoopShape shape;
+    mp_loop_shape(p->dp, &S, 1, p->num_sms, &shape);
+    if (shape.threads == 0) {
+        mpg_set_error("mp_decompose_static: no MP launch shape fits in shared memory");
+        return MP_ENOTCOMPAT;
+    }
+    CKS(launch_mp_loop(p->dp, d_sig, d_order, 1, K_max, thr_scale, 0, shape, st));
     if (n_atoms || stop_reason || final_snr_db) {
         DevSig out;
         CKS(cudaMemcpyAsync(&out, d_sig, sizeof(DevSig), cudaMemcpyDeviceToHost, st));

@@ -1,0 +1,71 @@
+"""GPU against the FP64 oracle on small versions of the paper's experiment
+set-ups (Sec. 6): white noise decomposed until the error estimate turns
+negative (Fig. 4 set-up), and single dictionaries of high redundancy and of
+many channels (Table 1 set-up), including frames of more than 128 chunks."""
+import numpy as np
+import pytest
+
+from oracle import cmp
+from paper_2202_12380_gb300 import inputs
+from tests.parity import compare
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts too
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2202_12380_gb300 import mpgabor as mg  # noqa: E402
+
+
+def _gpu(dicts, x, eps, K, snr):
+    plan = mg.mp_plan_create([g for g, _, _ in dicts], [a for _, a, _ in dicts],
+                             [M for _, _, M in dicts], eps)
+    xd = torch.from_numpy(x).cuda()
+    st = mg.mp_analyze(plan, [xd])
+    n, stop, q = mg.mp_run(st, K, snr)
+    atoms, errs = mg.mp_get_atoms(st, 0), mg.mp_get_errors(st, 0)
+    E0 = float(np.sum(x.astype(np.float64) ** 2))
+    y = torch.zeros_like(xd)
+    snr_true = mg.mp_synthesize(st, 0, y)
+    return atoms, errs, E0, int(stop[0]), snr_true
+
+
+def test_noise_until_negative_estimate():
+    """Fig. 4 set-up at L = 2^16, eps = 5e-3: both pursuits stop because E_k
+    turned negative; white noise is full of near ties, so what is compared
+    past the first one is the distribution: atoms to the stop within 3 %,
+    true quality within 0.3 dB."""
+    L = 1 << 16
+    x = inputs.as_f32(inputs.white_noise(L, inputs.seed_for(6, 1)))
+    dicts = [(inputs.blackman(M), M // 4, M) for M in (512, 1024, 2048)]
+    eps = 5e-3
+    ref = cmp.mp_coef(dicts, x.astype(np.float64), eps, 2 * L, 1000.0)
+    atoms, errs, E0, stop, snr_true = _gpu(dicts, x, eps, 2 * L, 1000.0)
+    assert ref.stop == cmp.STOP_NEGENERGY and stop == mg.MP_STOP_NEGENERGY
+    r = compare(atoms, errs, E0, ref, min_checked=20)
+    y = cmp.synth(dicts, ref, L)
+    snr_ref = 10 * np.log10(E0 / np.sum((x.astype(np.float64) - y) ** 2))
+    print("noise", r, "atoms gpu", atoms.size, "oracle", ref.n_atoms, "true SNR gpu", snr_true,
+          "oracle", snr_ref)
+    assert abs(atoms.size - ref.n_atoms) <= 0.03 * ref.n_atoms
+    assert abs(snr_true - snr_ref) < 0.3
+
+
+@pytest.mark.parametrize("M,ratio,L", [(1024, 32, 16384), (8192, 4, 16384), (16384, 4, 32768)])
+def test_single_dictionary_table1_shapes(M, ratio, L):
+    """Table 1 dictionaries: a = M/32 (redundancy 32), and M = 8192 / 16384
+    whose frames hold 129 / 257 chunks (more than the 128 a warp keeps in
+    registers).  The FP32 analysis error of a w-term frame product grows
+    like sqrt(w) 2^-24 of the frame norm, so for w > 4096 the per-coefficient
+    bar scales with sqrt(w / 4096) (times 2 for margin); the normwise error
+    stays within 1e-5."""
+    x = inputs.as_f32(inputs.mixture(L, 90 + ratio, fs=44100.0))
+    dicts = [(inputs.blackman(M), M // ratio, M)]
+    K = 300
+    ref = cmp.mp_coef(dicts, x.astype(np.float64), 1e-4, K, 200.0)
+    atoms, errs, E0, stop, _ = _gpu(dicts, x, 1e-4, K, 200.0)
+    rtol = 1e-5 * max(1.0, 2.0 * np.sqrt(M / 4096.0))
+    r = compare(atoms, errs, E0, ref, coef_rtol=rtol, min_checked=50)
+    print("M", M, "a", M // ratio, r)
+    assert r["normwise"] < 1e-5
