@@ -104,6 +104,14 @@ __device__ __forceinline__ void st_async8(unsigned raddr, unsigned lo, unsigned 
         : "memory");
 }
 
+// expect this iteration's candidate bytes and the selected coefficient
+__device__ __forceinline__ void arm_exchange(unsigned xb, unsigned vb, unsigned xbytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(xb), "r"(xbytes)
+                 : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(vb), "r"(8u)
+                 : "memory");
+}
+
 __device__ __forceinline__ bool xbar_try(unsigned addr, unsigned parity) {
     unsigned ok;
     asm volatile(
@@ -310,6 +318,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     __shared__ __align__(8) Key cand[2][16];   // CTA bests of the cluster, per parity
     __shared__ __align__(8) Key tmsg[2];       // time-limit message of CTA 0, per parity
     __shared__ __align__(8) float2 cval[2];    // selected coefficient, per parity
+    __shared__ __align__(8) float2 scoef[2];   // adjusted coefficient, per parity
+    __shared__ int sbad;                       // a bounded wait gave up
     __shared__ __align__(8) unsigned long long xbar[2];  // candidate barriers, per parity
     __shared__ __align__(8) unsigned long long vbar[2];  // coefficient barriers, per parity
     cg::cluster_group cluster = cg::this_cluster();
@@ -337,6 +347,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         tmsg[0] = tmsg[1] = 0ull;
         ndirty = 0;
+        sbad = 0;
     }
     __syncthreads();
     if (tid == 0) {
@@ -428,6 +439,11 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     // every CTA's barriers are initialised before anyone sends
     if (CS > 1) cluster.sync(); else __syncthreads();
 
+    // loop shape: warp 0 alone scans a small cluster top level; with a warp
+    // to spare (more warps than dictionaries) the last warp computes the
+    // coefficient and keeps the books while the others build the update
+    const bool w0scan = CS > 1 && T <= 256;
+    const bool early = NWARPS - 1 >= W;
     unsigned long long it = 0;  // iteration counter (exchange parities)
     for (;;) {
         const int par = (int)(it & 1);
@@ -435,7 +451,22 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         const unsigned vb = par ? vb1 : vb0;
         const unsigned xpar = (unsigned)((it >> 1) & 1);
         // ---- 1. scan of the top level, CTA best, cluster exchange ----------
-        {
+        Key best = 0ull;
+        if (w0scan) {
+            // a cluster CTA with at most 256 top-level keys: warp 0 scans them
+            // and sends, the other warps go straight to the wait
+            if (warp == 0) {
+                Key b[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) b[q] = lane + 32 * q < T ? top[lane + 32 * q] : 0ull;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) b[q] = b[q + 4] > b[q] ? b[q + 4] : b[q];
+                b[0] = b[2] > b[0] ? b[2] : b[0];
+                b[1] = b[3] > b[1] ? b[3] : b[1];
+                best = warp_max_key(b[1] > b[0] ? b[1] : b[0]);
+                if (lane == 0) arm_exchange(xb, vb, xbytes);
+            }
+        } else {
             // four independent running maxima, merged at the end
             Key b0 = 0ull, b1 = 0ull, b2 = 0ull, b3 = 0ull;
             int i = tid;
@@ -452,17 +483,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
             b0 = b2 > b0 ? b2 : b0;
             const Key r = warp_max_key(b0);
             if (lane == 0) wsel[warp] = r;
-            if (CS > 1 && tid == 0) {
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(xb),
-                             "r"(xbytes)
-                             : "memory");
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(vb),
-                             "r"(8u)
-                             : "memory");
-            }
+            if (CS > 1 && tid == 0) arm_exchange(xb, vb, xbytes);
+            __syncthreads();
+            best = warp_max_key(lane < NWARPS ? wsel[lane] : 0ull);
         }
-        __syncthreads();
-        Key best = warp_max_key(lane < NWARPS ? wsel[lane] : 0ull);
         if (CS > 1) {
             if (warp == 0) {
                 if (lane < CS) {
@@ -520,7 +544,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         float2 rho = make_float2(0.f, 0.f);
         const float2* psel = S.plane[u] + (long long)j * sd[u].Mrp + kk;
         if (CS == 1) {
-            rho = *psel;
+            if (!early || warp == NWARPS - 1) rho = *psel;
         } else if (warp == NWARPS - 1 && (j & (CS - 1)) == rank) {
             float2 r2 = make_float2(0.f, 0.f);
             if (lane == 0) r2 = *psel;
@@ -532,66 +556,94 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
             }
         }
 
-        // ---- 3. per-dictionary update descriptors ---------------------------
+        // ---- 3. per-dictionary update descriptors; 4. real-pair adjustment --
+        // eqs. dualatprod / projenfaster: coefficient and energy drop in FP32
+        // (gamma is zero away from m = 0 and m = M/2), E accumulated in FP64
+        // by the keeper thread, which also writes the atom and the next stop
+        // decision
+        auto adjust = [&](float2 r, float& cx, float& cy) {
+            float Edf;
+            if (edge) {
+                cx = r.x;
+                cy = 0.f;
+                Edf = r.x * r.x;
+            } else {
+                const float2 g = gamma_of(sd[u], sgam, kk);
+                if (g.x == 0.f && g.y == 0.f) {
+                    cx = r.x;
+                    cy = r.y;
+                    Edf = 2.f * fmaf(cx, cx, cy * cy);
+                } else {
+                    const float inv = 1.f / (1.f - fmaf(g.x, g.x, g.y * g.y));
+                    cx = (r.x - fmaf(g.x, r.x, g.y * r.y)) * inv;  // rho - conj(gamma) conj(rho)
+                    cy = (r.y - fmaf(g.y, r.x, -g.x * r.y)) * inv;
+                    const float c2 = fmaf(cx, cx, cy * cy), d2 = fmaf(cx, cx, -cy * cy);
+                    Edf = 2.f * (c2 + fmaf(g.x, d2, -2.f * g.y * cx * cy));
+                }
+            }
+            if (tid == KEEPER) {
+                E -= (double)Edf;
+                if (rank == 0) {
+                    mp_atom at;
+                    at.dict = u;
+                    at.m = kk;
+                    at.n = j;
+                    at.re = cx;
+                    at.im = cy;
+                    S.atoms[k] = at;
+                    S.errs[k] = E;
+                }
+                int s1 = 0;  // stop tests before the next selection
+                if (E <= 0.0) s1 = MP_STOP_NEGENERGY;
+                else if (E <= thr) s1 = MP_STOP_SNR;
+                else if (k + 1 >= kmax) s1 = MP_STOP_KMAX;
+                else if (resets && ((reset_it > 0 && k + 1 - k_out >= reset_it) ||
+                                    (reset_scale > 0.0 && E < E_out * reset_scale)))
+                    s1 = -3;  // reset pass (Alg. 2) before the next selection
+                sstop[(k + 1) & 1] = s1;
+            }
+        };
+        // bounded wait for the selected coefficient of a cluster
+        auto wait_coef = [&]() -> bool {
+            const unsigned long long w0 = gtimer();
+            while (!xbar_try(vb, xpar))
+                if (gtimer() - w0 > 2000000000ull) return false;
+            return true;
+        };
         for (int v = warp; v < W; v += NWARPS)
             build_vjob<POW2>(sd, sp, scls, W, S, u, kk, j, edge, v, rank, CS, cs_sh, lane, &vj[v],
                              chl + clo[v], tmk[v]);
+        float cx = 0.f, cy = 0.f;
+        if (early && warp == NWARPS - 1) {
+            bool ok = true;
+            if (CS > 1) {
+                ok = wait_coef();
+                rho = cval[par];
+            }
+            adjust(rho, cx, cy);
+            if (lane == 0) {
+                scoef[par] = make_float2(cx, cy);
+                if (!ok) sbad = 1;
+            }
+        }
         __syncthreads();
-        if (CS > 1) {
-            const unsigned long long w0 = gtimer();
-            while (!xbar_try(vb, xpar)) {
-                if (gtimer() - w0 > 2000000000ull) {
+        if (early) {
+            if (sbad) {
+                stop = -2;
+                break;
+            }
+            const float2 c2 = scoef[par];
+            cx = c2.x;
+            cy = c2.y;
+        } else {
+            if (CS > 1) {
+                if (!wait_coef()) {
                     stop = -2;
                     break;
                 }
+                rho = cval[par];
             }
-            rho = cval[par];
-            if (stop) break;
-        }
-
-        // ---- 4. real-pair adjustment and bookkeeping ------------------------
-        // eqs. dualatprod / projenfaster: coefficient and energy drop in FP32
-        // (gamma is zero away from m = 0 and m = M/2), E accumulated in FP64
-        const float rx = rho.x, ry = rho.y;
-        float cx, cy, Edf;
-        if (edge) {
-            cx = rx;
-            cy = 0.f;
-            Edf = rx * rx;
-        } else {
-            const float2 g = gamma_of(sd[u], sgam, kk);
-            if (g.x == 0.f && g.y == 0.f) {
-                cx = rx;
-                cy = ry;
-                Edf = 2.f * fmaf(cx, cx, cy * cy);
-            } else {
-                const float inv = 1.f / (1.f - fmaf(g.x, g.x, g.y * g.y));
-                cx = (rx - fmaf(g.x, rx, g.y * ry)) * inv;   // rho - conj(gamma) conj(rho)
-                cy = (ry - fmaf(g.y, rx, -g.x * ry)) * inv;
-                const float c2 = fmaf(cx, cx, cy * cy), d2 = fmaf(cx, cx, -cy * cy);
-                Edf = 2.f * (c2 + fmaf(g.x, d2, -2.f * g.y * cx * cy));
-            }
-        }
-        if (tid == KEEPER) {
-            E -= (double)Edf;
-            if (rank == 0) {
-                mp_atom at;
-                at.dict = u;
-                at.m = kk;
-                at.n = j;
-                at.re = cx;
-                at.im = cy;
-                S.atoms[k] = at;
-                S.errs[k] = E;
-            }
-            int s1 = 0;  // stop tests before the next selection
-            if (E <= 0.0) s1 = MP_STOP_NEGENERGY;
-            else if (E <= thr) s1 = MP_STOP_SNR;
-            else if (k + 1 >= kmax) s1 = MP_STOP_KMAX;
-            else if (resets && ((reset_it > 0 && k + 1 - k_out >= reset_it) ||
-                                (reset_scale > 0.0 && E < E_out * reset_scale)))
-                s1 = -3;  // reset pass (Alg. 2) before the next selection
-            sstop[(k + 1) & 1] = s1;
+            adjust(rho, cx, cy);
         }
         ++k;
 
