@@ -124,12 +124,13 @@ __device__ __forceinline__ bool xbar_try(unsigned addr, unsigned parity) {
 }
 
 // Dictionary v's update for the selected atom (u, k, j), built by one warp
-// (every lane computes the scalars; the lanes split the chunk list).  POW2:
+// (every lane computes the scalars and returns them; the lanes split the
+// chunk list).  POW2:
 // every M and a is a power of two, so the class, row and modulation indices
 // are shifts and masks.  tmk receives, per lane, which of the chunks
 // lane + 32 s (s < MAXL0) are touched.
 template <bool POW2>
-__device__ __forceinline__ void build_vjob(const DevDict* sd, const DevPair* sp,
+__device__ __forceinline__ VJob build_vjob(const DevDict* sd, const DevPair* sp,
                                            const DevClass* scls, int W, const DevSig& S, int u,
                                            int kk, int j, bool edge, int v, int rank, int CS,
                                            int cs_sh, int lane, VJob* out,
@@ -235,8 +236,8 @@ __device__ __forceinline__ void build_vjob(const DevDict* sd, const DevPair* sp,
         if (keep) clist[count + __popc(ball & ((1u << lane) - 1u))] = (unsigned short)c;
         count += __popc(ball);
     }
-    if (lane == 0) {
-        VJob J;
+    VJob J;
+    {
         J.act0 = act[0];
         J.act1 = act[1];
         J.Arow0 = Arow[0];
@@ -257,8 +258,9 @@ __device__ __forceinline__ void build_vjob(const DevDict* sd, const DevPair* sp,
         J.tile1 = tile[1];
         J.nlist = count;
         J.pad[0] = J.pad[1] = J.pad[2] = 0;
-        *out = J;
     }
+    if (lane == 0) *out = J;
+    return J;
 }
 
 // e^{i 2 pi q / M}, q < M, from the table of dictionary D: a quarter period
@@ -279,22 +281,37 @@ __device__ __forceinline__ float2 cis_at(const float2* t, const DevDict& D, int 
     return (k & 2) ? make_float2(-x, -y) : make_float2(x, y);
 }
 
-// per-term quantities of one frame: the tile column's first entry and the
-// weight c e^{i 2 pi q / M_u} (zero when the column misses the frame)
-__device__ __forceinline__ void term_frame(int act, int Acol, int C, int R, int qb, int dq,
-                                           long long tile, int n, int Nv, const DevDict& Du,
-                                           const float2* cis_u, float2 c, float2& w,
-                                           long long& tbase) {
-    int cc = n - Acol;
+// tile column of a term for frame n: its first entry in the tile pool, or -1
+// when the column misses the frame; cc is the column index
+__device__ __forceinline__ long long term_col(int act, int Acol, int C, int R, long long tile, int n,
+                                              int Nv, int& cc) {
+    cc = n - Acol;
     cc += cc < 0 ? Nv : 0;
-    const bool hit = act && cc < C;
+    return (act && cc < C) ? tile + (long long)cc * R : -1ll;
+}
+
+// weight c e^{i 2 pi q / M_u} of column cc, q = qb + cc dq (mod M_u); zero
+// when the column misses the frame
+__device__ __forceinline__ float2 term_weight(long long tbase, int cc, int qb, int dq,
+                                              const DevDict& Du, const float2* cis_u, float2 c) {
+    if (tbase < 0) return make_float2(0.f, 0.f);
     int q;
     if (Du.Mmask) q = (int)(((unsigned)qb + (unsigned)cc * (unsigned)dq) & (unsigned)Du.Mmask);
     else q = (int)(((long long)qb + (long long)cc * dq) % Du.M);
-    w = hit ? cmul(c, cis_at(cis_u, Du, hit ? q : 0)) : make_float2(0.f, 0.f);
-    tbase = tile + (long long)cc * R;
-    if (!hit) tbase = -1;
+    return cmul(c, cis_at(cis_u, Du, q));
 }
+
+// one frame job in registers: the frame, its level-0 keys, the columns of
+// both terms, and the loads of one batch of touched chunks
+struct JobCtx {
+    int v, n, nb;
+    int cc0, cc1;
+    long long tb0, tb1;
+    Key l0v[MAXL0];
+    int cq[CB];
+    float2 val[CB], h0[CB], h1[CB];
+    bool hit[CB];
+};
 
 template <int NT, bool POW2>
 __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
@@ -406,6 +423,142 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     for (int i = tid; i < ((T + 31) >> 5); i += NT) dbits[i] = 0u;
     // dictionary bases of the flat index, one per lane (lane w < W)
     const unsigned fb_l = lane < W ? S.fbase[lane] : 0xffffffffu;
+    constexpr bool PREF = NT == 128;
+    const float2* __restrict__ tiles = P.tiles;
+
+    // frame jobs (step 5).  job_begin: the frame n = nstart + f CS of
+    // dictionary v, its level-0 keys, both terms' tile columns and the loads
+    // of the first batch of touched chunks (nothing here needs the
+    // coefficient).  job_end: the update (eq. fastkernupdate with the
+    // modulation of eq. hkj), new chunk keys, further batches, the frame
+    // maximum and the top level.
+    auto load_batch = [&](JobCtx& x, const VJob& J, int b0) {
+        const DevDict& Dv = sd[x.v];
+        const int Mv = Dv.M, Mr = Dv.Mr;
+        const unsigned short* lst = chl + clo[x.v];
+        const float2* prow = S.plane[x.v] + (long long)x.n * Dv.Mrp;
+        const int nb = min(CB, J.nlist - b0);  // uniform
+        x.nb = nb;
+        auto load_slot = [&](int q) {
+            x.cq[q] = q < nb ? (int)lst[b0 + q] : -1;
+            const int m = x.cq[q] * CHUNK + lane;
+            const bool ok = x.cq[q] >= 0;
+            x.val[q] = ok ? prow[ok ? m : 0] : make_float2(0.f, 0.f);
+            int i0 = m - J.Arow0;
+            i0 += i0 < 0 ? Mv : 0;
+            int i1 = m - J.Arow1;
+            i1 += i1 < 0 ? Mv : 0;
+            const bool s0 = ok && m < Mr && x.tb0 >= 0 && i0 < J.R0;
+            const bool s1 = ok && m < Mr && x.tb1 >= 0 && i1 < J.R1;
+            x.h0[q] = s0 ? __ldg(tiles + x.tb0 + i0) : make_float2(0.f, 0.f);
+            x.h1[q] = s1 ? __ldg(tiles + x.tb1 + i1) : make_float2(0.f, 0.f);
+            x.hit[q] = s0 || s1;
+        };
+        // all loads first (one round trip), the second pair only when the
+        // batch holds more than two chunks
+        load_slot(0);
+        load_slot(1);
+        if (nb > 2) {
+            load_slot(2);
+            load_slot(3);
+        } else {
+            x.cq[2] = x.cq[3] = -1;
+        }
+    };
+    auto job_begin = [&](JobCtx& x, const VJob& J, int v, int f) {
+        const DevDict& Dv = sd[v];
+        const int Nv = (int)S.N[v];
+        int n = J.nstart + f * CS;
+        n -= (n >= Nv) ? Nv : 0;
+        n -= (n >= Nv) ? Nv : 0;
+        x.v = v;
+        x.n = n;
+        const Key* l0row = S.l0[v] + (long long)n * Dv.nch;
+#pragma unroll
+        for (int q = 0; q < MAXL0; ++q) {
+            const int c = lane + 32 * q;
+            x.l0v[q] = c < Dv.nch ? l0row[c] : 0ull;
+        }
+        x.tb0 = term_col(J.act0, J.Acol0, J.C0, J.R0, J.tile0, n, Nv, x.cc0);
+        x.tb1 = term_col(J.act1, J.Acol1, J.C1, J.R1, J.tile1, n, Nv, x.cc1);
+        load_batch(x, J, 0);
+    };
+    auto job_end = [&](JobCtx& x, const VJob& J, float2 c_main, float2 c_conj, int u) {
+        const int v = x.v, n = x.n;
+        const DevDict& Dv = sd[v];
+        const int Mr = Dv.Mr, nch = Dv.nch;
+        const float2* cis_u = scis + sd[u].cis_off;
+        const float2 w0 = term_weight(x.tb0, x.cc0, J.qb0, J.dq0, sd[u], cis_u, c_main);
+        const float2 w1 = term_weight(x.tb1, x.cc1, J.qb1, J.dq1, sd[u], cis_u, c_conj);
+        Key* l0row = S.l0[v] + (long long)n * nch;
+        float2* prow = S.plane[v] + (long long)n * Dv.Mrp;
+        const unsigned fn = S.fbase[v] + ((unsigned)n << Dv.msh);
+        const unsigned tm = tmk[v][lane];
+        Key tmax = 0ull;  // maximum of the touched chunks' new keys
+        Key e[CB];
+        // update and key of one slot
+        auto update_slot = [&](int q) {
+            const int m = x.cq[q] * CHUNK + lane;
+            float2 x2 = x.val[q];
+            const float2 d0 = cmul(w0, x.h0[q]);
+            x2.x -= d0.x;
+            x2.y -= d0.y;
+            const float2 d1 = cmul(w1, x.h1[q]);
+            x2.x -= d1.x;
+            x2.y -= d1.y;
+            if (x.hit[q]) prow[m] = x2;
+            e[q] = (x.cq[q] >= 0 && m < Mr) ? make_key_sel(x2, fn + m, m, Dv, sgam, P.pedantic)
+                                            : 0ull;
+        };
+        for (int b0 = 0; b0 < J.nlist; b0 += CB) {
+            if (b0 > 0) load_batch(x, J, b0);
+            const int nb = x.nb;
+            update_slot(0);
+            update_slot(1);
+            warp_max_key2(e[0], e[1]);
+            if (lane == 0) l0row[x.cq[0]] = e[0];
+            tmax = e[0] > tmax ? e[0] : tmax;
+            if (nb > 1) {
+                if (lane == 1) l0row[x.cq[1]] = e[1];
+                tmax = e[1] > tmax ? e[1] : tmax;
+            }
+            if (nb > 2) {
+                update_slot(2);
+                update_slot(3);
+                warp_max_key2(e[2], e[3]);
+                if (lane == 2) l0row[x.cq[2]] = e[2];
+                tmax = e[2] > tmax ? e[2] : tmax;
+                if (nb > 3) {
+                    if (lane == 3) l0row[x.cq[3]] = e[3];
+                    tmax = e[3] > tmax ? e[3] : tmax;
+                }
+            }
+        }
+        // frame maximum: the touched chunks' new keys and the untouched
+        // chunks' stored ones
+        Key fb = tmax;
+#pragma unroll
+        for (int q = 0; q < MAXL0; ++q)
+            if (!((tm >> q) & 1u) && x.l0v[q] > fb) fb = x.l0v[q];
+        if (nch > 32 * MAXL0) {
+            __syncwarp();  // this warp's level-0 stores are visible to its loads
+            for (int c = lane + 32 * MAXL0; c < nch; c += 32) fb = l0row[c] > fb ? l0row[c] : fb;
+        }
+        const Key fr = warp_max_key(fb);
+        if (lane == 0) {
+            S.l1[v][n] = fr;
+            if (CS > 1) {
+                top[ltb[v] + (n >> cs_sh)] = fr;
+            } else if (gsh == 0) {
+                top[ltb[v] + n] = fr;
+            } else {
+                const int gi = ltb[v] + (n >> gsh);
+                const unsigned bit = 1u << (gi & 31);
+                if (!(atomicOr(&dbits[gi >> 5], bit) & bit))
+                    dlist[atomicAdd(&ndirty, 1)] = (unsigned short)gi;
+            }
+        }
+    };
 
     long long k = S.k;
     // FP64 work stays in one thread (the FP64 pipe is narrow on this part):
@@ -421,7 +574,6 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     const long long k_out = S.k_out;
     const double E_out = S.E_out;
     const unsigned long long t_start = gtimer();
-    const float2* __restrict__ tiles = P.tiles;
     const unsigned xbytes = (unsigned)(CS * sizeof(Key)) + (budget_ns > 0 ? 8u : 0u);
     int stop = 0;
     if (tid == KEEPER) {
@@ -610,9 +762,20 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                 if (gtimer() - w0 > 2000000000ull) return false;
             return true;
         };
-        for (int v = warp; v < W; v += NWARPS)
-            build_vjob<POW2>(sd, sp, scls, W, S, u, kk, j, edge, v, rank, CS, cs_sh, lane, &vj[v],
-                             chl + clo[v], tmk[v]);
+        // a warp that builds dictionary v's descriptor also issues the loads
+        // of v's first owned frame (128-thread CTAs, which have the
+        // registers): they fly while the barrier and the coefficient wait
+        JobCtx px;
+        bool pref = false;
+        for (int v = warp; v < W; v += NWARPS) {
+            const VJob Jv = build_vjob<POW2>(sd, sp, scls, W, S, u, kk, j, edge, v, rank, CS,
+                                             cs_sh, lane, &vj[v], chl + clo[v], tmk[v]);
+            if (PREF && v == warp && Jv.cnt > 0) {
+                __syncwarp();  // the chunk list was written by this warp's lanes
+                job_begin(px, Jv, v, 0);
+                pref = true;
+            }
+        }
         float cx = 0.f, cy = 0.f;
         if (early && warp == NWARPS - 1) {
             bool ok = true;
@@ -647,137 +810,29 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         }
         ++k;
 
-        // ---- 5. frame jobs, dealt from one flat index -----------------------
+        // ---- 5. frame jobs: the prefetched one, then the rest dealt from one
+        //         flat index (warps without a prefetched job first) ----------
         {
             const float2 c_main = make_float2(cx, cy), c_conj = make_float2(cx, -cy);
-            const float2* cis_u = scis + sd[u].cis_off;
-            // inclusive prefix of the job counts, lane w holding dictionary w's
-            int pre = lane < W ? vj[lane].cnt : 0;
+            if (pref) job_end(px, vj[px.v], c_main, c_conj, u);
+            // remaining jobs per dictionary (lane w < W), inclusive prefix
+            int cw = lane < W ? vj[lane].cnt : 0;
+            const int off = (PREF && lane < NWARPS && cw > 0) ? 1 : 0;  // prefetched
+            int pre = cw - off;
 #pragma unroll
             for (int o = 1; o < MAXW; o <<= 1) {
                 const int y = __shfl_up_sync(FULL, pre, o);
                 if (lane >= o) pre += y;
             }
-            const int njobs = __shfl_sync(FULL, pre, W - 1);
-            for (int g = warp; g < njobs; g += NWARPS) {
+            const int nrem = __shfl_sync(FULL, pre, W - 1);
+            const int first = PREF ? ((warp - W) % NWARPS + NWARPS) % NWARPS : warp;
+            for (int g = first; g < nrem; g += NWARPS) {
                 const int v = __popc(__ballot_sync(FULL, lane < W && g >= pre));
-                const int f = g - (v > 0 ? __shfl_sync(FULL, pre, (v + 31) & 31) : 0);
-                const VJob& J = vj[v];
-                const DevDict& Dv = sd[v];
-                const int Nv = (int)S.N[v];
-                const int Mv = Dv.M, Mr = Dv.Mr, nch = Dv.nch;
-                int n = J.nstart + f * CS;
-                n -= (n >= Nv) ? Nv : 0;
-                n -= (n >= Nv) ? Nv : 0;
-                // level-0 keys of the whole frame (touched ones are recomputed)
-                Key* l0row = S.l0[v] + (long long)n * nch;
-                Key l0v[MAXL0];
-#pragma unroll
-                for (int q = 0; q < MAXL0; ++q) {
-                    const int c = lane + 32 * q;
-                    l0v[q] = c < nch ? l0row[c] : 0ull;
-                }
-                float2* prow = S.plane[v] + (long long)n * Dv.Mrp;
-                float2 w0, w1;
-                long long tb0, tb1;
-                term_frame(J.act0, J.Acol0, J.C0, J.R0, J.qb0, J.dq0, J.tile0, n, Nv, sd[u], cis_u,
-                           c_main, w0, tb0);
-                term_frame(J.act1, J.Acol1, J.C1, J.R1, J.qb1, J.dq1, J.tile1, n, Nv, sd[u], cis_u,
-                           c_conj, w1, tb1);
-                const unsigned short* lst = chl + clo[v];
-                const unsigned fn = S.fbase[v] + ((unsigned)n << Dv.msh);
-                const unsigned tm = tmk[v][lane];
-                Key tmax = 0ull;  // maximum of the touched chunks' new keys
-                for (int b0 = 0; b0 < J.nlist; b0 += CB) {
-                    const int nb = min(CB, J.nlist - b0);  // uniform
-                    int cq[CB];
-                    float2 val[CB], h0[CB], h1[CB];
-                    bool hit[CB];
-                    // loads of one slot: the plane chunk and both terms' tile entries
-                    auto load_slot = [&](int q) {
-                        cq[q] = q < nb ? (int)lst[b0 + q] : -1;
-                        const int m = cq[q] * CHUNK + lane;
-                        const bool ok = cq[q] >= 0;
-                        val[q] = ok ? prow[ok ? m : 0] : make_float2(0.f, 0.f);
-                        int i0 = m - J.Arow0;
-                        i0 += i0 < 0 ? Mv : 0;
-                        int i1 = m - J.Arow1;
-                        i1 += i1 < 0 ? Mv : 0;
-                        const bool s0 = ok && m < Mr && tb0 >= 0 && i0 < J.R0;
-                        const bool s1 = ok && m < Mr && tb1 >= 0 && i1 < J.R1;
-                        h0[q] = s0 ? __ldg(tiles + tb0 + i0) : make_float2(0.f, 0.f);
-                        h1[q] = s1 ? __ldg(tiles + tb1 + i1) : make_float2(0.f, 0.f);
-                        hit[q] = s0 || s1;
-                    };
-                    Key e[CB];
-                    // update and key of one slot
-                    auto update_slot = [&](int q) {
-                        const int m = cq[q] * CHUNK + lane;
-                        float2 x2 = val[q];
-                        const float2 d0 = cmul(w0, h0[q]);
-                        x2.x -= d0.x;
-                        x2.y -= d0.y;
-                        const float2 d1 = cmul(w1, h1[q]);
-                        x2.x -= d1.x;
-                        x2.y -= d1.y;
-                        if (hit[q]) prow[m] = x2;
-                        e[q] = (cq[q] >= 0 && m < Mr)
-                                   ? make_key_sel(x2, fn + m, m, Dv, sgam, P.pedantic)
-                                   : 0ull;
-                    };
-                    // all loads first (one round trip), the second pair only
-                    // when the batch holds more than two chunks
-                    load_slot(0);
-                    load_slot(1);
-                    if (nb > 2) {
-                        load_slot(2);
-                        load_slot(3);
-                    }
-                    update_slot(0);
-                    update_slot(1);
-                    warp_max_key2(e[0], e[1]);
-                    if (lane == 0) l0row[cq[0]] = e[0];
-                    tmax = e[0] > tmax ? e[0] : tmax;
-                    if (nb > 1) {
-                        if (lane == 1) l0row[cq[1]] = e[1];
-                        tmax = e[1] > tmax ? e[1] : tmax;
-                    }
-                    if (nb > 2) {
-                        update_slot(2);
-                        update_slot(3);
-                        warp_max_key2(e[2], e[3]);
-                        if (lane == 2) l0row[cq[2]] = e[2];
-                        tmax = e[2] > tmax ? e[2] : tmax;
-                        if (nb > 3) {
-                            if (lane == 3) l0row[cq[3]] = e[3];
-                            tmax = e[3] > tmax ? e[3] : tmax;
-                        }
-                    }
-                }
-                // frame maximum: the touched chunks' new keys and the untouched
-                // chunks' stored ones
-                Key fb = tmax;
-#pragma unroll
-                for (int s = 0; s < MAXL0; ++s)
-                    if (!((tm >> s) & 1u) && l0v[s] > fb) fb = l0v[s];
-                if (nch > 32 * MAXL0) {
-                    __syncwarp();  // this warp's level-0 stores are visible to its loads
-                    for (int c = lane + 32 * MAXL0; c < nch; c += 32) fb = l0row[c] > fb ? l0row[c] : fb;
-                }
-                const Key fr = warp_max_key(fb);
-                if (lane == 0) {
-                    S.l1[v][n] = fr;
-                    if (CS > 1) {
-                        top[ltb[v] + (n >> cs_sh)] = fr;
-                    } else if (gsh == 0) {
-                        top[ltb[v] + n] = fr;
-                    } else {
-                        const int gi = ltb[v] + (n >> gsh);
-                        const unsigned bit = 1u << (gi & 31);
-                        if (!(atomicOr(&dbits[gi >> 5], bit) & bit))
-                            dlist[atomicAdd(&ndirty, 1)] = (unsigned short)gi;
-                    }
-                }
+                const int f = g - (v > 0 ? __shfl_sync(FULL, pre, (v + 31) & 31) : 0) +
+                              __shfl_sync(FULL, off, v);
+                JobCtx x;
+                job_begin(x, vj[v], v, f);
+                job_end(x, vj[v], c_main, c_conj, u);
             }
         }
         __syncthreads();
