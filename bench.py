@@ -362,7 +362,7 @@ def run_batched(args, mg, torch, ws=1, rank=0):
     if ws > 1:
         xs = [xs[i] for i in partition([len(x) for x in xs], ws)[rank]]
     stream = torch.cuda.Stream()
-    aflag = mg.MP_ANALYSIS_BF16X3 if args.analysis == "bf16x3" else mg.MP_ANALYSIS_FP32
+    aflag = mg.MP_ANALYSIS_BF16X3 if args.batched_analysis == "bf16x3" else mg.MP_ANALYSIS_FP32
     plan = mg.mp_plan_create([d[0] for d in dicts], [d[1] for d in dicts], [d[2] for d in dicts],
                              cfg["eps"], aflag, stream)
     xd = [torch.from_numpy(x).cuda() for x in xs]
@@ -404,7 +404,7 @@ def run_batched(args, mg, torch, ws=1, rank=0):
     peak, _ = _peaks()
     # the slowest rank's step against the atoms of all ranks (one rank: itself)
     t_max, atoms_all = reduce_totals(step / 1e3, float(n.sum()), device="cuda")
-    out = {"workload": "batch256", "analysis": args.analysis, "signals": n_all,
+    out = {"workload": "batch256", "analysis": args.batched_analysis, "signals": n_all,
            "L_total": L_all, "launch_shape": list(shape),
            "autotune_ms": {"%dx%d" % k: round(v, 3) for k, v in tune_ms.items()},
            "cuda_graph": True, "atoms_per_step": int(atoms_all), "ms_per_step": t_max * 1e3,
@@ -487,6 +487,8 @@ def main():
                     help="analysis precision (bf16x3: split-BF16 DFT-GEMM on tcgen05)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--batched-analysis", default="bf16x3", choices=["fp32", "bf16x3"],
+                    help="analysis precision of the batched form")
     ap.add_argument("--batched-steps", type=int, default=3)
     ap.add_argument("--tune-atoms", type=int, default=0,
                     help="atoms per launch-shape probe of the batched autotuner "
