@@ -27,7 +27,8 @@ namespace mpg {
 
 constexpr int MAXW = 8;          // dictionaries per plan
 constexpr int CHUNK = 32;        // bins per level-0 entry (one warp)
-constexpr int TOPCAP = 16384;    // top-level keys held in shared memory per CTA
+constexpr int TOPCAP = 16384;    // top-level keys held in shared memory per single CTA
+constexpr int TOPCAP_CLUSTER = 24576;  // own frames a cluster CTA may hold (if they fit)
 
 using Key = unsigned long long;
 

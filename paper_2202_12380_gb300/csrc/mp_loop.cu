@@ -1013,12 +1013,12 @@ bool mp_loop_shape_ok(const DevPlan& P, const DevSig* hs, int B, int threads, in
         }
         lt = t > lt ? t : lt;
     }
-    if (lt > TOPCAP) return false;
+    if (lt > TOPCAP_CLUSTER) return false;
     const size_t sm = mp_loop_smem_bytes(P, lt, threads, c);
     if (sm > SMEM_MAX || mp_loop_max_clusters(threads, c, sm) < 1) return false;
     out->threads = threads;
     out->cs = c;
-    out->topcap = TOPCAP;
+    out->topcap = TOPCAP_CLUSTER;
     out->smem = sm;
     return true;
 }
@@ -1039,10 +1039,15 @@ void mp_loop_shape(const DevPlan& P, const DevSig* hs, int B, int num_sms, LoopS
         if (t == 1 || t == 2 || t == 4 || t == 8 || t == 16) c = t;
     }
     *out = LoopShape();
-    // a cluster CTA runs only a few frame jobs per iteration: one warp per
-    // scheduler keeps the redundant selection off each other's issue slots
-    for (; c > 1; c >>= 1)
-        if (mp_loop_shape_ok(P, hs, B, nt_override ? nt_override : 128, c, out)) return;
+    // a cluster CTA runs only a few frame jobs per iteration: with up to
+    // three dictionaries one warp per scheduler (and a spare warp) is fastest;
+    // with more dictionaries the jobs and descriptors need more warps
+    // (measured on GB300: 3 dictionaries 128 threads, 5 dictionaries 512)
+    const int nt_cluster = nt_override ? nt_override : (P.W <= 3 ? 128 : 512);
+    for (; c > 1; c >>= 1) {
+        if (mp_loop_shape_ok(P, hs, B, nt_cluster, c, out)) return;
+        if (!nt_override && nt_cluster != 128 && mp_loop_shape_ok(P, hs, B, 128, c, out)) return;
+    }
     if (mp_loop_shape_ok(P, hs, B, nt_override ? nt_override : nt, 1, out)) return;
     for (int t : {512, 256, 128})
         if (mp_loop_shape_ok(P, hs, B, t, 1, out)) return;
