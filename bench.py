@@ -404,6 +404,9 @@ def run_batched(args, mg, torch, ws=1, rank=0):
     peak, _ = _peaks()
     # the slowest rank's step against the atoms of all ranks (one rank: itself)
     t_max, atoms_all = reduce_totals(step / 1e3, float(n.sum()), device="cuda")
+    # measured DRAM bytes of one launch (ncu summary, while the source matches)
+    traffic = _profile_traffic(os.path.join(ROOT, "paper_2202_12380_gb300", "csrc", "mp_loop.cu"),
+                               "batch256")
     out = {"workload": "batch256", "analysis": args.batched_analysis, "signals": n_all,
            "L_total": L_all, "launch_shape": list(shape),
            "autotune_ms": {"%dx%d" % k: round(v, 3) for k, v in tune_ms.items()},
@@ -413,6 +416,8 @@ def run_batched(args, mg, torch, ws=1, rank=0):
            "parallelism": "signals partitioned over %d ranks" % ws if ws > 1 else "single",
            "scaling": "strong" if ws > 1 else None,
            "mp_loop_hbm_frac": alg / (loop / 1e3) / 1e9 / peak,
+           "mp_loop_traffic": traffic,
+           "mp_loop_dram_frac": (traffic / (loop / 1e3) / 1e9 / peak) if traffic else None,
            "stops": {str(k): int(v) for k, v in zip(*np.unique(stops, return_counts=True))}}
     state.close()
     plan.close()
