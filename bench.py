@@ -175,19 +175,32 @@ def update_bytes(mg, plan, state, atoms_per_sig):
     return total
 
 
+def code_sha256(path):
+    """sha256 of a C/CUDA source with // comments, trailing blanks and empty
+    lines removed: it changes with the code, not with its comments."""
+    lines = []
+    for line in open(path, encoding="utf-8").read().splitlines():
+        i = line.find("//")
+        if i >= 0:
+            line = line[:i]
+        line = line.rstrip()
+        if line:
+            lines.append(line)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
 def _profile_traffic(kernel_file, workload):
     """dram bytes per launch of the MP loop from the committed ncu summary,
-    or None when the kernel source changed since it was captured."""
+    or None when the kernel's code changed since it was captured."""
     path = os.path.join(ROOT, "profiles", "mp_loop_%s.md" % workload)
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    m = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    m = re.search(r"code_sha256:\s*([0-9a-f]{64})", text)
     t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
     if not (m and t):
         return None
-    cur = hashlib.sha256(open(kernel_file, "rb").read()).hexdigest()
-    return float(t.group(1)) if cur == m.group(1) else None
+    return float(t.group(1)) if code_sha256(kernel_file) == m.group(1) else None
 
 
 def _peaks():

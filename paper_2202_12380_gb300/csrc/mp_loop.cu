@@ -4,39 +4,46 @@
 // domain update of every dictionary -> max-tree repair, entirely on the
 // device.
 //
-// Max tree (Sec. 5.1).  Level 0 (per frame and 32-bin chunk) and level 1
-// (per frame) live in global memory next to the coefficient planes; the top
-// level (one Entry per frame, or per group of 2^gshift frames) lives in
-// shared memory and is scanned by the whole CTA every iteration, so there is
-// no further level to maintain.
+// Max tree (Sec. 5.1), keys only (score bits and inverted flat index).
+// Level 0 (per frame and 32-bin chunk) and level 1 (per frame) live in
+// global memory next to the coefficient planes; the top level (one key per
+// frame, or per group of 2^gshift frames of a single CTA whose frames do not
+// fit) lives in shared memory and is scanned every iteration.  The selected
+// coefficient itself is read from its plane.
 //
 // One iteration:
-//   1. every thread scans its share of the top level; warp bests are reduced
-//      to the CTA best (shared memory + barrier);
+//   1. the CTA's best key: warp 0 alone scans a cluster CTA's top level,
+//      otherwise every thread scans its share and a barrier combines them;
 //   2. with a cluster, each CTA sends its best to every CTA of the cluster
 //      (st.async into distributed shared memory, completing bytes on the
 //      receiver's mbarrier) and waits, bounded, for all of them; every warp
-//      then takes the same selection and adjusts the coefficient to the
-//      real-pair coefficient (eqs. dualatprod / projenfaster); one thread
-//      keeps E in FP64 and writes the atom list;
-//   3. warp v builds dictionary v's update for this iteration -- the class
+//      then decodes the same selection;
+//   3. the selected coefficient: a single CTA reads it from its plane; in a
+//      cluster the CTA owning the frame reads it and sends it to every CTA
+//      (second mbarrier), overlapped with step 4;
+//   4. warp v builds dictionary v's update for this iteration -- the class
 //      tiles of the atom and of its conjugate partner, their first row and
 //      column, the modulation index of column 0 and its step, the frames of
-//      the column hull owned by this CTA, and the list of touched 32-bin
-//      chunks -- into shared memory; barrier;
-//   4. the frame jobs of all dictionaries are dealt to the warps from one
-//      flat index.  A job loads the frame's level-0 entries together with
+//      the column hull owned by this CTA, the list of touched 32-bin chunks
+//      and the lanes' touched-chunk masks -- into shared memory; in
+//      128-thread CTAs it also issues the loads of its dictionary's first
+//      frame job; a spare warp (more warps than dictionaries) adjusts the
+//      coefficient to the real-pair coefficient (eqs. dualatprod /
+//      projenfaster), keeps E in FP64, writes the atom and the next stop
+//      decision; barrier;
+//   5. frame jobs: the prefetched one, then the rest dealt to the warps from
+//      one flat index.  A job loads the frame's level-0 keys together with
 //      the touched chunks of the plane and the matching tile entries,
 //      subtracts both terms (eq. fastkernupdate with the modulation of eq.
 //      hkj, looked up in an FP64-rounded table), recomputes the touched
-//      chunks' level-0 entries, the frame's level-1 entry and its top-level
-//      slot; barrier;
-//   5. (single CTA with grouped top level) the groups of touched frames are
+//      chunks' level-0 keys, the frame's level-1 key and its top-level slot;
+//      barrier;
+//   6. (single CTA with grouped top level) the groups of touched frames are
 //      rebuilt, one thread per group; barrier.
 //
 // Clusters.  A signal may be given a thread-block cluster of CS CTAs (on CS
 // SMs) instead of one CTA: frame n of every dictionary belongs to CTA
-// n mod CS, which holds its top-level entry and runs its frame jobs.  The
+// n mod CS, which holds its top-level key and runs its frame jobs.  The
 // time limit is decided by CTA 0 and sent with the candidates, so all CTAs
 // leave the loop in the same iteration.
 #include <cooperative_groups.h>
