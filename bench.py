@@ -320,7 +320,10 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_baseline:
-        cpu = cpu_baseline(args.workload, args.cpu_atoms)
+        g_atoms = mg.mp_get_atoms(state, 0)
+        g_errs = mg.mp_get_errors(state, 0)
+        g_E0 = float(g_errs[-1] * 10 ** (snrs[0] / 10)) if g_errs.size else 1.0
+        cpu = cpu_baseline(args.workload, args.cpu_atoms, g_atoms, g_errs, g_E0)
 
     line = {
         "metric": METRIC,
@@ -439,21 +442,50 @@ def run_batched(args, mg, torch, ws=1, rank=0):
 
 # -------------------------------------------------------------- CPU arm -----
 
-def _oracle_sample(workload, atoms):
+def _oracle_sample(workload, atoms, keep=False):
     from oracle import cmp
     cfg, dicts, xs = _workload(workload)
     x = xs[0].astype(np.float64)
     t0 = time.perf_counter()
     res = cmp.mp_coef(dicts, x, cfg["eps"], atoms, cfg["snr_db"])
     dt = time.perf_counter() - t0
-    return res.n_atoms, dt
+    return (res.n_atoms, dt, res) if keep else (res.n_atoms, dt)
 
 
-def cpu_baseline(workload, atoms):
-    n, dt = _oracle_sample(workload, atoms)
-    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "FP64 C oracle (coefficient-domain MP, 1 thread): analysis + first %d atoms "
-                      "of the %s signal, %.1f s" % (n, workload, dt)}
+def cpu_baseline(workload, atoms, gpu_atoms=None, gpu_errs=None, gpu_E0=None):
+    """The oracle timed on the host; with the GPU decomposition of the same
+    signal also its error against the oracle over the common prefix."""
+    n, dt, ref = _oracle_sample(workload, atoms, keep=True)
+    out = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "FP64 C oracle (coefficient-domain MP, 1 thread): analysis + first %d atoms "
+                     "of the %s signal, %.1f s" % (n, workload, dt)}
+    if gpu_atoms is not None:
+        out["oracle_error"] = oracle_error(gpu_atoms, gpu_errs, gpu_E0, ref)
+    return out
+
+
+def oracle_error(atoms, errs, E0, ref):
+    """Sequence agreement, coefficient error and SNR-curve deviation of a GPU
+    decomposition against the FP64 oracle's, up to the oracle's first near
+    tie (relative gap of the two largest |rho| below 1e-6)."""
+    gap = (ref.s1 - ref.s2) / np.where(ref.s1 > 0, ref.s1, 1.0)
+    ties = np.where(gap < 1e-6)[0]
+    tie = int(ties[0]) if ties.size else ref.n_atoms
+    k = min(atoms.size, ref.n_atoms)
+    same = (atoms["dict"][:k] == ref.dict[:k]) & (atoms["m"][:k] == ref.m[:k]) & \
+        (atoms["n"][:k] == ref.n[:k])
+    div = int(np.argmin(same)) if not same.all() else k
+    upto = min(tie, div)
+    c = atoms["re"][:upto].astype(np.float64) + 1j * atoms["im"][:upto].astype(np.float64)
+    rel = np.abs(c - ref.c[:upto]) / np.abs(ref.c[:upto]) if upto else np.zeros(1)
+    dsnr = np.abs(10 * np.log10(E0 / errs[:k]) - 10 * np.log10(ref.E0 / ref.E[:k]))
+    return {"first_near_tie": tie, "first_divergence": div, "compared": upto,
+            "coef_rel_max": float(rel.max()),
+            "coef_normwise": float(np.linalg.norm(c - ref.c[:upto]) / np.linalg.norm(ref.c[:upto]))
+            if upto else 0.0,
+            "snr_db_max_to_tie": float(dsnr[:upto].max()) if upto else 0.0,
+            "snr_db_max_common": float(dsnr.max()) if k else 0.0,
+            "atoms_gpu": int(atoms.size), "atoms_oracle": int(ref.n_atoms)}
 
 
 def run_reference(args):
