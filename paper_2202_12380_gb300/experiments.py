@@ -13,8 +13,12 @@ stand-ins for the recordings.
   paper) and atoms/s.  The paper's piano recording is replaced by the
   seeded mixture of ``inputs.mixture``.
 
-Run ``python -m paper_2202_12380_gb300.experiments noise|table1``; each
-configuration prints one JSON line.
+* ``noise_resets`` (Sec. 6.1, second experiment): the same noise with resets
+  after a fixed number of selections, the true quality after K selections
+  compared across thresholds.
+
+Run ``python -m paper_2202_12380_gb300.experiments noise|resets|table1``;
+each configuration prints one JSON line.
 """
 from __future__ import annotations
 
@@ -43,9 +47,9 @@ PAPER_TABLE1 = {  # (M, M/a) -> seconds for 180 000 selections, i5-4570, one cor
     ("multi", 4): 10.6, ("multi", 8): 20.9}
 
 
-def _decompose(dicts, x, eps, kmax, snr_db, flags=0):
+def _decompose(dicts, x, eps, kmax, snr_db, flags=0, reset_every=0):
     """Plan (untimed), then analysis + pursuit timed with CUDA events;
-    returns (n_atoms, stop, seconds, true snr dB)."""
+    returns (n_atoms, stop, seconds, true snr dB, launch shape)."""
     import torch
 
     plan = mg.mp_plan_create([g for g, _, _ in dicts], [a for _, a, _ in dicts],
@@ -55,7 +59,12 @@ def _decompose(dicts, x, eps, kmax, snr_db, flags=0):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     st = mg.mp_analyze(plan, [xd])
-    mg.mp_run_async(st, kmax, snr_db)
+    if reset_every:
+        # resets are host-driven passes between MP launches (Alg. 2)
+        mg.mp_state_set_resets(st, reset_every)
+        mg.mp_run(st, kmax, snr_db)
+    else:
+        mg.mp_run_async(st, kmax, snr_db)
     e1.record()
     torch.cuda.synchronize()
     n, stop, _ = mg.mp_get_status(st)
@@ -84,6 +93,21 @@ def noise_convergence(eps_list=(1e-4, 1e-3, 5e-3), L=NOISE_L, seed=NOISE_SEED):
                "paper": {"atoms": paper[0], "quality_db": paper[1]} if paper else None}
 
 
+def noise_resets(K=3_000_000, settings=((1e-4, 0), (1e-3, 2_000_000), (5e-3, 1_000_000)),
+                 L=NOISE_L, seed=NOISE_SEED):
+    """Sec. 6.1 second experiment on the noise signal: resets after a fixed
+    number of selections (the paper: 2e6 at eps = 1e-3, 1e6 at 5e-3), K
+    selections; the true quality after K should agree across thresholds."""
+    x = inputs.white_noise(L, seed)
+    dicts = [(inputs.blackman(M), M // 4, M) for M in (512, 1024, 2048)]
+    for eps, every in settings:
+        n, stop, secs, snr, shape = _decompose(dicts, x, eps, K, 1000.0, reset_every=every)
+        yield {"experiment": "noise_resets", "eps": eps, "reset_every": every, "L": L,
+               "atoms": n, "stop": {mg.MP_STOP_KMAX: "K", mg.MP_STOP_NEGENERGY: "E_k<0"}.get(stop, stop),
+               "true_snr_db": snr, "seconds": secs, "atoms_per_s": n / secs,
+               "launch_shape": list(shape)}
+
+
 def table1(K=180000, L=TABLE1_L, seed=TABLE1_SEED, Ms=(512, 1024, 2048, 4096, 8192, 16384),
            ratios=(4, 8, 16, 32), multi=True):
     """Table 1 set-up on the synthetic stand-in; yields one dict per row."""
@@ -104,13 +128,15 @@ def table1(K=180000, L=TABLE1_L, seed=TABLE1_SEED, Ms=(512, 1024, 2048, 4096, 81
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["noise", "table1"])
+    ap.add_argument("which", choices=["noise", "resets", "table1"])
     ap.add_argument("--eps", type=float, nargs="*", default=None)
     ap.add_argument("--ratios", type=int, nargs="*", default=None)
     ap.add_argument("--no-multi", dest="multi", action="store_false")
     args = ap.parse_args()
     if args.which == "noise":
         it = noise_convergence(tuple(args.eps) if args.eps else (1e-4, 1e-3, 5e-3))
+    elif args.which == "resets":
+        it = noise_resets()
     else:
         it = table1(ratios=tuple(args.ratios) if args.ratios else (4, 8, 16, 32),
                     multi=args.multi)
