@@ -170,8 +170,11 @@ int mp_state_set_time_limit(mp_state* state, double seconds);
 /*
  * Launch shape of the MP loop (tuning): threads per CTA (128, 256 or 512)
  * and CTAs per signal (thread-block cluster of 1, 2, 4, 8 or 16; more
- * than one needs every N_w = L/a_w divisible by it).  The default is chosen
- * from the number of signals; threads = cluster = 0 restores it.  Returns
+ * than one needs every N_w = L/a_w divisible by it and each CTA's share of
+ * the frames to fit in shared memory).  The default is chosen from the
+ * number of signals and dictionaries (up to 8 signals: 16-CTA clusters,
+ * 128 threads per CTA for up to three dictionaries, 512 for more; many
+ * signals: one CTA each); threads = cluster = 0 restores it.  Returns
  * MP_EINVAL for a shape this state cannot run.  mp_state_get_launch reports
  * the current shape.  Results do not depend on the shape.
  */
