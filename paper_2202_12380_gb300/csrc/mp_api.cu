@@ -454,11 +454,13 @@ int read_status(mp_state* s, int64_t* n_atoms, int* stop, double* snr, bool* tim
 
 extern "C" int mp_analyze(const mp_plan* plan, mp_state** state, int B, const float* const* x_dev,
                           const int64_t* L) {
+    mpg::NvtxRange nvtx_range("mp_analyze");
     return analyze_impl(plan, state, B, x_dev, L, cudaMemcpyDeviceToDevice);
 }
 
 extern "C" int mp_analyze_host(const mp_plan* plan, mp_state** state, int B,
                                const float* const* x_host, const int64_t* L) {
+    mpg::NvtxRange nvtx_range("mp_analyze_host");
     return analyze_impl(plan, state, B, x_host, L, cudaMemcpyHostToDevice);
 }
 
@@ -489,6 +491,7 @@ extern "C" int mp_state_set_time_limit(mp_state* s, double seconds) {
 }
 
 extern "C" int mp_run_async(mp_state* s, int64_t K_max, double target_snr_db) {
+    mpg::NvtxRange nvtx_range("mp_run_async");
     if (!s || K_max < 0 || std::isnan(target_snr_db)) {
         mpg_set_error("mp_run: bad argument");
         return MP_EINVAL;
@@ -542,6 +545,7 @@ extern "C" int mp_get_status(mp_state* s, int64_t* n_atoms, int* stop, double* s
 
 extern "C" int mp_run(mp_state* s, int64_t K_max, double target_snr_db, int64_t* n_atoms,
                       int* stop_reason, double* final_snr_db) {
+    mpg::NvtxRange nvtx_range("mp_run");
     for (;;) {
         int rc = mp_run_async(s, K_max, target_snr_db);
         if (rc) return rc;
@@ -637,6 +641,7 @@ extern "C" int mp_get_errors(const mp_state* s, int sig, double* E, int64_t cap,
 }
 
 extern "C" int mp_synthesize(const mp_state* s, int sig, float* y, double* true_snr_db) {
+    mpg::NvtxRange nvtx_range("mp_synthesize");
     if (!s || sig < 0 || sig >= s->B || !y) {
         mpg_set_error("mp_synthesize: bad argument");
         return MP_EINVAL;

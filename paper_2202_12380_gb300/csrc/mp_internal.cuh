@@ -19,6 +19,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "mpgabor.h"
@@ -164,6 +165,17 @@ size_t mp_loop_smem_bytes(const DevPlan& P, int T, int threads, int cs);
 int mp_loop_threads(int nsig, int num_sms);
 int mp_loop_max_clusters(int threads, int cs, size_t smem);
 
+}  // namespace mpg
+
+namespace mpg {
+// NVTX range over one C-ABI call (visible in nsys / ncu timelines; NVTX v3
+// is header-only and costs nothing when no tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 }  // namespace mpg
 
 // error helpers (mp_api.cu)

@@ -234,6 +234,7 @@ bool mpg::encode_bf16_map(void* map, const void* base, unsigned long long inner,
 extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows,
                               const int* win_len, const int* a, const int* M, double kern_thr,
                               unsigned flags, void* cuda_stream) {
+    mpg::NvtxRange nvtx_range("mp_plan_create");
     if (!out || W < 1 || W > MAXW || !windows || !win_len || !a || !M) {
         mpg_set_error("mp_plan_create: bad arguments (W must be 1..%d)", MAXW);
         return MP_EINVAL;

@@ -102,6 +102,7 @@ int scratch_address(unsigned char** out) {
 extern "C" int mp_decompose_static(const mp_plan* p, const float* x_dev, int64_t L, int64_t K_max,
                                    double target_snr_db, mp_atom* atoms_dev, double* errors_dev,
                                    int64_t* n_atoms, int* stop_reason, double* final_snr_db) {
+    mpg::NvtxRange nvtx_range("mp_decompose_static");
     if (!p || !x_dev || !atoms_dev || L <= 0 || K_max < 1 || std::isnan(target_snr_db)) {
         mpg_set_error("mp_decompose_static: bad argument (need plan, signal, atom buffer, "
                       "L > 0, K_max >= 1)");
