@@ -14,13 +14,6 @@ __device__ __forceinline__ long long lmod(long long x, long long m) {
     return r < 0 ? r + m : r;
 }
 
-// selection key: score bits in the high word, inverted flat index low
-__device__ __forceinline__ unsigned long long make_key(float2 v, unsigned flat) {
-    float s = fmaf(v.x, v.x, v.y * v.y);
-    return ((unsigned long long)__float_as_uint(s) << 32) |
-           (unsigned long long)(0xffffffffu - flat);
-}
-
 __device__ __forceinline__ float2 gamma_of(const DevDict& D, const float2* gam, int k) {
     if (k < D.gam_lo) return gam[D.gam_off + k];
     if (k >= D.Mr - D.gam_hi) return gam[D.gam_off + D.gam_lo + (k - (D.Mr - D.gam_hi))];
@@ -41,6 +34,8 @@ __device__ __forceinline__ float pair_score(float2 v, int m, const DevDict& D, c
     return fmaxf(0.f, 2.f * (c2 + fmaf(g.x, d2, -2.f * g.y * cx * cy)));
 }
 
+// selection key: score bits in the high word (|rho|^2, or the pair energy
+// drop when pedantic), inverted flat index in the low word
 __device__ __forceinline__ unsigned long long make_key_sel(float2 v, unsigned flat, int m,
                                                            const DevDict& D, const float2* gam,
                                                            int pedantic) {
