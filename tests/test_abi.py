@@ -98,3 +98,13 @@ def test_plan_validation_is_host_side(libpath, case, expect):
     rc, msg = _create(wins, a, M, eps)
     assert rc == expect, (rc, msg)
     assert msg
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: without the built library every call raises."""
+    from paper_2202_12380_gb300 import mpgabor
+
+    monkeypatch.setattr(mpgabor, "_lib", None)
+    monkeypatch.setattr(mpgabor, "lib_path", lambda: str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        mpgabor.lib()
