@@ -114,3 +114,76 @@ def mp_definition(dicts, x, kmax, pedantic=False):
         atoms.append((w, m, n, c))
         energies.append(float(r @ r))
     return atoms, np.array(energies), r
+
+
+def full_multi(dicts, L):
+    """Concatenated full dictionary (every m = 0..M-1) of all dictionaries,
+    columns in (w, n, m) order, with a map from (w, m, n) to the column."""
+    cols, index, o = [], {}, 0
+    for w, (g, a, M) in enumerate(dicts):
+        N = L // a
+        D = gabor_matrix(g, a, M, L)
+        # gabor_matrix orders columns m + n M, i.e. (n, m) order already
+        cols.append(D)
+        for n in range(N):
+            for m in range(M):
+                index[(w, m, n)] = o + m + n * M
+        o += M * N
+    return np.concatenate(cols, axis=1), index
+
+
+def mp_truncated_gram(dicts, x, eps, kmax):
+    """Coefficient-domain matching pursuit of Alg. 1 with the truncated Gram
+    matrix of eq. truncgram, built explicitly.
+
+    G = D^* D over the full multi-Gabor dictionary (every frequency, so the
+    conjugate partners are columns too), G(q, p) = <d_p, d_q>; G_eps keeps
+    the entries with |G| > eps and sets the others to 0.  rho_0 = D^* x.
+    Per step (before it: stop once the estimate E_k <= 0):
+      * select p = argmax |rho(p)|^2 over the reduced dictionary
+        (m = 0..M/2; ties: first in (w, n, m) order);
+      * m in {0, M/2}: the atom is real, c = Re rho(p), energy drop c^2,
+        rho -= c G_eps(., p);
+      * otherwise, with the partner pbar = (w, M - m, n) and
+        gamma = G_eps(pbar, p) = <d_p, conj d_p> (zero when truncated),
+        c = (rho(p) - conj(gamma) conj(rho(p))) / (1 - |gamma|^2)
+        (eq. dualatprod), energy drop 2 |c|^2 + 2 Re(c^2 gamma)
+        (eq. projenfaster), rho -= c G_eps(., p) + conj(c) G_eps(., pbar);
+      * E_{k+1} = E_k - energy drop.
+    Windows are unit-norm, so <d, d> = 1.  Returns the atoms (w, m, n, c)
+    and the estimates E_1..E_K."""
+    x = np.asarray(x, np.float64)
+    L = x.size
+    D, index = full_multi(dicts, L)
+    G = D.conj().T @ D
+    G[np.abs(G) <= eps] = 0.0
+    rho = D.conj().T @ x
+    labels = []
+    for w, (g, a, M) in enumerate(dicts):
+        labels += [(w, m, n) for n in range(L // a) for m in range(M // 2 + 1)]
+    red = np.array([index[lab] for lab in labels])
+    E = float(x @ x)
+    atoms, Es = [], []
+    for _ in range(kmax):
+        if E <= 0.0:
+            break
+        s = np.abs(rho[red]) ** 2
+        q = int(np.argmax(s))
+        w, m, n = labels[q]
+        M = dicts[w][2]
+        p = red[q]
+        r0 = rho[p]
+        if m == 0 or 2 * m == M:
+            c = complex(r0.real, 0.0)
+            drop = c.real ** 2
+            rho = rho - c * G[:, p]
+        else:
+            pb = index[(w, M - m, n)]
+            gam = G[pb, p]
+            c = (r0 - np.conj(gam) * np.conj(r0)) / (1.0 - abs(gam) ** 2)
+            drop = 2.0 * abs(c) ** 2 + 2.0 * (c * c * gam).real
+            rho = rho - c * G[:, p] - np.conj(c) * G[:, pb]
+        E -= drop
+        atoms.append((w, m, n, complex(c)))
+        Es.append(E)
+    return atoms, np.array(Es)

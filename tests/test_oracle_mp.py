@@ -273,3 +273,52 @@ def test_pedantic_coef_eps0_equals_plain():
     assert np.array_equal(a.dict, b.dict) and np.array_equal(a.m, b.m)
     assert np.array_equal(a.n, b.n)
     assert np.max(np.abs(a.c - b.c) / np.abs(a.c)) < 1e-9
+
+
+def _gram_layout(case):
+    if case == "two":
+        return 96, [(inputs.blackman(16), 4, 16), (inputs.hann(32), 8, 32)]
+    if case == "fig2":
+        return 512, [(inputs.blackman(32), 16, 32), (inputs.hann(8), 4, 8)]
+    # asymmetric window: complex <d, conj d>, so gamma and its conjugation
+    # in eq. dualatprod matter
+    g = np.random.default_rng(7).uniform(0.2, 1.0, 32)
+    return 256, [(g / np.linalg.norm(g), 8, 32), (inputs.blackman(64), 16, 64)]
+
+
+def test_truncated_gram_eps0_is_mp_by_definition():
+    """The explicit G-based Alg. 1 with G_0 = D^* D reproduces MP by
+    definition (numpy least squares), so its closed forms are pinned."""
+    L, dicts = _gram_layout("asym")
+    x = inputs.mixture(L, 21, fs=8000.0)
+    K = 60
+    at, E = explicit.mp_truncated_gram(dicts, x, 0.0, K)
+    ref, energies, _ = explicit.mp_definition(dicts, x, K)
+    assert [a[:3] for a in at] == [a[:3] for a in ref]
+    assert max(abs(a[3] - b[3]) for a, b in zip(at, ref)) < 1e-10
+    assert np.max(np.abs(E - energies[1:])) < 1e-10 * energies[0]
+
+
+@pytest.mark.parametrize("case", ["two", "fig2", "asym"])
+@pytest.mark.parametrize("eps", [1e-3, 1e-2])
+def test_coef_eps_matches_explicit_truncated_gram(case, eps):
+    """eps > 0: the C oracle's kernel-based G_eps (thresholded cross-kernels,
+    the landing of Alg. 3, the conjugate term, gamma from the own kernel)
+    equals Alg. 1 with the explicitly thresholded D^* D (eq. truncgram)."""
+    L, dicts = _gram_layout(case)
+    x = inputs.mixture(L, 17, fs=8000.0)
+    K = 120 if L > 96 else 60
+    at, E = explicit.mp_truncated_gram(dicts, x, eps, K)
+    res = cmp.mp_coef(dicts, x, eps, K, 400.0, fullscan=True)
+    assert res.n_atoms == len(at) > 0
+    assert [(int(a), int(b), int(c)) for a, b, c in zip(res.dict, res.m, res.n)] == \
+        [a[:3] for a in at]
+    c = np.array([a[3] for a in at])
+    assert np.max(np.abs(res.c - c)) < 1e-12 * np.max(np.abs(c)) * 100
+    assert np.max(np.abs(res.E - E)) < 1e-12 * res.E0
+    # the truncation is active: the eps = 0 pursuit differs
+    at0, _ = explicit.mp_truncated_gram(dicts, x, 0.0, K)
+    c0 = np.array([a[3] for a in at0])
+    k = min(len(at0), len(at))
+    assert [a[:3] for a in at0[:k]] != [a[:3] for a in at[:k]] or \
+        np.max(np.abs(c0[:k] - c[:k])) > 1e-6 * np.max(np.abs(c))
