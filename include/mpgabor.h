@@ -71,8 +71,12 @@ enum {
     MP_ANALYSIS_FP32 = 0,   /* analysis as an FP32 DFT-GEMM on the SIMT cores (default) */
     MP_ANALYSIS_BF16X3 = 1, /* analysis as a split-BF16 three-product DFT-GEMM on tcgen05;
                                needs every a a multiple of 64 and every w/2 a multiple of a */
-    MP_PEDANTIC = 2         /* select by the real-pair energy drop of eq. projenfaster
+    MP_PEDANTIC = 2,        /* select by the real-pair energy drop of eq. projenfaster
                                ("pedantic", Sec. 5) instead of |rho|^2 */
+    MP_COEF_FP64 = 4        /* FP64 coefficient planes, kernel tiles, modulation and
+                               <d, conj d> tables, FP64 analysis (DFT-GEMM on the FP64
+                               pipe): the paper's precision (Sec. 6), for parity runs;
+                               not combinable with MP_ANALYSIS_BF16X3 */
 };
 
 /*
@@ -87,8 +91,9 @@ enum {
  *   cuda_stream cudaStream_t used by every call on this plan (NULL: legacy)
  * Computes on the device, in FP64, every cross-kernel h_{u,v} on the common
  * grid (a_min, M_max), thresholds it, splits it into dense FP32 tiles per
- * grid alignment class, and derives <d, conj d> for every own-dictionary
- * frequency.  Cost and memory are independent of the signal length.
+ * grid alignment class (and FP64 tiles with MP_COEF_FP64), and derives
+ * <d, conj d> for every own-dictionary frequency.  Cost and memory are
+ * independent of the signal length.
  * Returns MP_EINVAL / MP_ENOTCOMPAT on bad input, MP_ECUDA / MP_ENOMEM on
  * device failure; *out is set only on success.  Synchronises the stream.
  */
@@ -214,14 +219,14 @@ void mp_state_destroy(mp_state* state);
  * Allocation-free decomposition of one signal (no counterpart in the paper:
  * it is an operational variant of mp_analyze + mp_run).
  *
- * For callers that cannot call cudaMalloc while they decompose: work issued
- * inside a CUDA stream capture (cudaMalloc is not a stream operation and
- * breaks the capture), real-time audio threads that must not block on the
- * device allocator (cudaMalloc may synchronise the device), and processes
- * held to a fixed device-memory budget.  The plan is created beforehand (that
- * call allocates); this call then allocates nothing: the coefficient planes,
- * max trees and bookkeeping live in one file-scope device array of 32 MiB
- * that every GPU loading the library holds until the process exits.
+ * For callers that cannot call cudaMalloc while they decompose: real-time
+ * audio threads that must not block on the device allocator (cudaMalloc may
+ * synchronise the device and take unbounded time), and processes held to a
+ * fixed device-memory budget or whose device memory belongs to their own
+ * pool allocator.  The plan is created beforehand (that call allocates);
+ * this call then allocates nothing: the coefficient planes, max trees and
+ * bookkeeping live in one file-scope device array of 32 MiB that every GPU
+ * loading the library holds until the process exits.
  *   x_dev       device pointer to L floats (input)
  *   atoms_dev   device buffer of K_max mp_atom (output, atoms in order)
  *   errors_dev  device buffer of K_max doubles for E_k (output) or NULL
@@ -229,9 +234,12 @@ void mp_state_destroy(mp_state* state);
  *               are NULL the call is asynchronous on the plan's stream,
  *               otherwise it synchronises the stream and fills them
  * Same method, kernels and results as mp_analyze + mp_run on one signal
- * (no time limit).  Returns MP_EINVAL with a message if the signal needs
- * more than the 32 MiB array (about L = 2^18 with three dictionaries of
- * 512..2048 channels fits); use mp_analyze / mp_run for larger inputs.
+ * with the FP32 analysis (no time limit, no resets).  Returns
+ * MP_ENOTCOMPAT for a plan made with MP_ANALYSIS_BF16X3 (this call runs the
+ * FP32 analysis only), MP_EINVAL if the current device is not the plan's,
+ * and MP_EINVAL with a message if the signal needs more than the 32 MiB
+ * array (about L = 2^18 with three dictionaries of 512..2048 channels fits);
+ * use mp_analyze / mp_run for those.
  * The first call on each device resolves the array's device address
  * (cudaGetSymbolAddress) -- make that first call before any stream capture.
  * All calls on a device share the array and each call rewrites every part

@@ -6,9 +6,10 @@
 // is one real GEMM per dictionary: C = A B with A[2m + {0,1}][i] the
 // windowed cosine / negated sine rows (built by the plan) and B[i][n] =
 // x(n a + i - w/2) the frames, gathered on the fly from the signal (no
-// framed copy is materialised).  The FP32 path below runs it on the SIMT
-// cores with register blocking; the epilogue writes complex rows of the
-// frame-major coefficient plane directly.
+// framed copy is materialised).  The SIMT path below runs it with register
+// blocking in FP32 (float2 planes) or, for MP_COEF_FP64 plans, in FP64
+// (double2 planes); the epilogue writes complex rows of the frame-major
+// coefficient plane directly.
 #include <cuda_runtime.h>
 
 #include "mp_common_dev.cuh"
@@ -29,13 +30,70 @@ __device__ __forceinline__ int find_sig(const long long* prefix, int nsig, long 
     return lo;
 }
 
-__global__ void __launch_bounds__(256) k_analysis_sgemm(const float* __restrict__ A, int Kp, int w,
-                                                        int a, int Mrp, int nsig,
-                                                        const long long* __restrict__ tprefix,
-                                                        const DevSig* __restrict__ sigs, int dict,
-                                                        int flagged) {
-    __shared__ __align__(16) float As[BK][BM];
-    __shared__ __align__(16) float Bs[BK][BN];
+// eight consecutive matrix entries (k .. k + 7 of one row)
+__device__ __forceinline__ void load8(const float* p, float o[8]) {
+    const float4 a0 = *reinterpret_cast<const float4*>(p);
+    const float4 a1 = *reinterpret_cast<const float4*>(p + 4);
+    o[0] = a0.x; o[1] = a0.y; o[2] = a0.z; o[3] = a0.w;
+    o[4] = a1.x; o[5] = a1.y; o[6] = a1.z; o[7] = a1.w;
+}
+__device__ __forceinline__ void load8(const double* p, double o[8]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const double2 v = reinterpret_cast<const double2*>(p)[q];
+        o[2 * q] = v.x;
+        o[2 * q + 1] = v.y;
+    }
+}
+
+// shared-memory reads of the inner product: 8 rows and 4 frames (vector loads)
+__device__ __forceinline__ void lds84(const float* a, const float* b, float r8[8], float c4[4]) {
+    const float4 x0 = *reinterpret_cast<const float4*>(a);
+    const float4 x1 = *reinterpret_cast<const float4*>(a + 4);
+    const float4 y0 = *reinterpret_cast<const float4*>(b);
+    r8[0] = x0.x; r8[1] = x0.y; r8[2] = x0.z; r8[3] = x0.w;
+    r8[4] = x1.x; r8[5] = x1.y; r8[6] = x1.z; r8[7] = x1.w;
+    c4[0] = y0.x; c4[1] = y0.y; c4[2] = y0.z; c4[3] = y0.w;
+}
+__device__ __forceinline__ void lds84(const double* a, const double* b, double r8[8],
+                                      double c4[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const double2 x = reinterpret_cast<const double2*>(a)[q];
+        r8[2 * q] = x.x;
+        r8[2 * q + 1] = x.y;
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const double2 y = reinterpret_cast<const double2*>(b)[q];
+        c4[2 * q] = y.x;
+        c4[2 * q + 1] = y.y;
+    }
+}
+
+// four bins (re, im pairs) of one frame into the plane
+__device__ __forceinline__ void store4(float2* dst, const float v[8], int left) {
+    if (left >= 4) {
+        reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
+        for (int b = 0; b < left; ++b) dst[b] = make_float2(v[2 * b], v[2 * b + 1]);
+    }
+}
+__device__ __forceinline__ void store4(double2* dst, const double v[8], int left) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+        if (b < left) dst[b] = make_double2(v[2 * b], v[2 * b + 1]);
+}
+
+template <typename T, typename C2>
+__global__ void __launch_bounds__(256) k_analysis_gemm(const T* __restrict__ A, int Kp, int w,
+                                                       int a, int Mrp, int nsig,
+                                                       const long long* __restrict__ tprefix,
+                                                       const DevSig* __restrict__ sigs, int dict,
+                                                       int flagged) {
+    __shared__ __align__(16) T As[BK][BM];
+    __shared__ __align__(16) T Bs[BK][BN];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const long long gt = blockIdx.x;
@@ -48,73 +106,56 @@ __global__ void __launch_bounds__(256) k_analysis_sgemm(const float* __restrict_
     const long long n0 = (gt - tprefix[s]) * BN;
     const int r0 = blockIdx.y * BM;
 
-    float acc[8][4];
+    T acc[8][4];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 
     // A tile loader: row r0 + (tid >> 1), 8 consecutive k from (tid & 1) * 8
     const int ar = tid >> 1, ak = (tid & 1) * 8;
-    const float* Arow = A + (long long)(r0 + ar) * Kp;
+    const T* Arow = A + (long long)(r0 + ar) * Kp;
     // B tile loader: k = tid & 15, frames (tid >> 4) + 16 q
     const int bk = tid & 15, bn = tid >> 4;
 
     for (int k0 = 0; k0 < Kp; k0 += BK) {
-        float4 a0 = *reinterpret_cast<const float4*>(Arow + k0 + ak);
-        float4 a1 = *reinterpret_cast<const float4*>(Arow + k0 + ak + 4);
-        float bv[4];
+        T a8[8];
+        load8(Arow + k0 + ak, a8);
+        T bv[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             long long n = n0 + bn + 16 * q;
             int i = k0 + bk;
-            float v = 0.f;
-            if (n < N && i < w) v = __ldg(x + lmod(n * a + i - w / 2, L));
+            T v = T(0);
+            if (n < N && i < w) v = (T)__ldg(x + lmod(n * a + i - w / 2, L));
             bv[q] = v;
         }
         __syncthreads();
-        As[ak + 0][ar] = a0.x;
-        As[ak + 1][ar] = a0.y;
-        As[ak + 2][ar] = a0.z;
-        As[ak + 3][ar] = a0.w;
-        As[ak + 4][ar] = a1.x;
-        As[ak + 5][ar] = a1.y;
-        As[ak + 6][ar] = a1.z;
-        As[ak + 7][ar] = a1.w;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) As[ak + q][ar] = a8[q];
 #pragma unroll
         for (int q = 0; q < 4; ++q) Bs[bk][bn + 16 * q] = bv[q];
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            float4 x0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
-            float4 x1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
-            float4 y0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-            float ar8[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-            float bc4[4] = {y0.x, y0.y, y0.z, y0.w};
+            T ar8[8], bc4[4];
+            lds84(&As[kk][ty * 8], &Bs[kk][tx * 4], ar8, bc4);
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ar8[i], bc4[j], acc[i][j]);
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(ar8[i], bc4[j], acc[i][j]);
         }
     }
     // epilogue: rows ty*8 .. +7 are bins (r0 + ty*8)/2 .. +3 (re, im pairs)
     const int m0 = (r0 + ty * 8) >> 1;
-    float2* plane = S.plane[dict];
+    C2* plane = reinterpret_cast<C2*>(S.plane[dict]);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         long long n = n0 + tx * 4 + j;
         if (n >= N) continue;
-        float2* dst = plane + n * Mrp + m0;
-        if (m0 + 3 < Mrp) {
-            float4 v0 = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
-            float4 v1 = make_float4(acc[4][j], acc[5][j], acc[6][j], acc[7][j]);
-            reinterpret_cast<float4*>(dst)[0] = v0;
-            reinterpret_cast<float4*>(dst)[1] = v1;
-        } else {
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-                if (m0 + b < Mrp) dst[b] = make_float2(acc[2 * b][j], acc[2 * b + 1][j]);
-        }
+        const T v[8] = {acc[0][j], acc[1][j], acc[2][j], acc[3][j],
+                        acc[4][j], acc[5][j], acc[6][j], acc[7][j]};
+        store4(plane + n * Mrp + m0, v, Mrp - m0);
     }
 }
 
@@ -152,7 +193,8 @@ __global__ void __launch_bounds__(1024) k_energy(DevSig* sigs) {
 }
 
 // level 0 (per 32-bin chunk) and level 1 (per frame) of dictionary `dict`,
-// one warp per frame
+// one warp per frame (C2: float2 or double2 planes)
+template <typename C2>
 __global__ void k_tree_build(DevPlan P, const DevSig* __restrict__ sigs, int nsig,
                              const long long* __restrict__ fprefix, long long total, int dict,
                              int flagged) {
@@ -164,14 +206,15 @@ __global__ void k_tree_build(DevPlan P, const DevSig* __restrict__ sigs, int nsi
     if (flagged && !S.reanalyze) return;
     const long long n = gw - fprefix[s];
     const DevDict& D = P.d[dict];
-    const float2* row = S.plane[dict] + n * D.Mrp;
+    const C2* row = reinterpret_cast<const C2*>(S.plane[dict]) + n * D.Mrp;
+    const C2* gam = plane_tables<C2>::gam(P);
     Key* l0 = S.l0[dict] + n * D.nch;
     const unsigned fb = S.fbase[dict] + ((unsigned)n << D.msh);
     Key best = 0ull;
     for (int ch = 0; ch < D.nch; ++ch) {
         const int m = ch * CHUNK + lane;
-        const float2 v = row[m];
-        const Key k = (m < D.Mr) ? make_key_sel(v, fb + m, m, D, P.gam, P.pedantic) : 0ull;
+        const C2 v = row[m];
+        const Key k = (m < D.Mr) ? make_key_sel(v, fb + m, m, D, gam, P.pedantic) : 0ull;
         const Key r = warp_max_key(k);
         if (lane == 0) l0[ch] = r;
         best = r > best ? r : best;
@@ -217,8 +260,19 @@ cudaError_t launch_analysis_sgemm(const float* A, int Arows, int Kp, int w_len, 
                                   int flagged) {
     if (total_frame_tiles <= 0) return cudaSuccess;
     dim3 grid((unsigned)total_frame_tiles, (unsigned)(Arows / BM));
-    k_analysis_sgemm<<<grid, 256, 0, st>>>(A, Kp, w_len, a, Mrp, nsig, d_tile_prefix, d_sigs, dict,
-                                           flagged);
+    k_analysis_gemm<float, float2><<<grid, 256, 0, st>>>(A, Kp, w_len, a, Mrp, nsig,
+                                                         d_tile_prefix, d_sigs, dict, flagged);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_analysis_dgemm(const double* A, int Arows, int Kp, int w_len, int a, int Mrp,
+                                  int nsig, const long long* d_tile_prefix, const DevSig* d_sigs,
+                                  int dict, long long total_frame_tiles, cudaStream_t st,
+                                  int flagged) {
+    if (total_frame_tiles <= 0) return cudaSuccess;
+    dim3 grid((unsigned)total_frame_tiles, (unsigned)(Arows / BM));
+    k_analysis_gemm<double, double2><<<grid, 256, 0, st>>>(A, Kp, w_len, a, Mrp, nsig,
+                                                           d_tile_prefix, d_sigs, dict, flagged);
     return cudaGetLastError();
 }
 
@@ -237,8 +291,13 @@ cudaError_t launch_tree_build(const DevPlan& P, const DevSig* d_sigs, int nsig,
                               cudaStream_t st, int flagged) {
     if (total_frames <= 0) return cudaSuccess;
     const int wpb = 8;
-    k_tree_build<<<(unsigned)((total_frames + wpb - 1) / wpb), wpb * 32, 0, st>>>(
-        P, d_sigs, nsig, d_frame_prefix, total_frames, dict, flagged);
+    const unsigned grid = (unsigned)((total_frames + wpb - 1) / wpb);
+    if (P.fp64)
+        k_tree_build<double2><<<grid, wpb * 32, 0, st>>>(P, d_sigs, nsig, d_frame_prefix,
+                                                         total_frames, dict, flagged);
+    else
+        k_tree_build<float2><<<grid, wpb * 32, 0, st>>>(P, d_sigs, nsig, d_frame_prefix,
+                                                        total_frames, dict, flagged);
     return cudaGetLastError();
 }
 

@@ -157,6 +157,7 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
     s->reset_it = 0;
     s->reset_db = 0.0;
     const int W = p->W;
+    const size_t esz = (p->flags & MP_COEF_FP64) ? sizeof(double2) : sizeof(float2);
     // layout of every signal inside one pool
     size_t off = 0;
     std::vector<size_t> o_plane(B * W), o_l0(B * W), o_l1(B * W), o_x(B), o_r(B), o_y(B);
@@ -174,7 +175,7 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
             fb += (unsigned)(S.N[w] << D.msh);
             F += S.N[w];
             o_plane[b * W + w] = off;
-            off = align256(off + sizeof(float2) * S.N[w] * D.Mrp);
+            off = align256(off + esz * S.N[w] * D.Mrp);
             o_l0[b * W + w] = off;
             off = align256(off + sizeof(Key) * S.N[w] * D.nch);
             o_l1[b * W + w] = off;
@@ -366,6 +367,10 @@ int analysis_pass(mp_state* s, int flagged) {
             CKR(launch_analysis_tc(maps, p->Arows[w], p->Kp64[w], D.a, D.Mrp, B, s->d_tc_prefix[w],
                                    s->d_brow + (size_t)w * B, s->d_sigs, w, s->total_tc_tiles[w],
                                    s->d_err, st, flagged));
+        } else if (p->flags & MP_COEF_FP64) {
+            CKR(launch_analysis_dgemm(p->d_A64[w], p->Arows[w], p->Akp[w], D.wlen, D.a, D.Mrp, B,
+                                      s->d_tile_prefix[w], s->d_sigs, w, s->total_tiles[w], st,
+                                      flagged));
         } else {
             CKR(launch_analysis_sgemm(p->d_A[w], p->Arows[w], p->Akp[w], D.wlen, D.a, D.Mrp, B,
                                       s->d_tile_prefix[w], s->d_sigs, w, s->total_tiles[w], st,
@@ -474,6 +479,16 @@ extern "C" int mp_state_coefficients(const mp_state* s, int sig, int w, float* h
     if (cap < 2 * N * D.Mr) {
         mpg_set_error("mp_state_coefficients: buffer too small");
         return MP_EINVAL;
+    }
+    if (s->plan->flags & MP_COEF_FP64) {
+        // FP64 planes: copied as they are, rounded to float on the host
+        std::vector<double> tmp((size_t)2 * N * D.Mr);
+        CKR(cudaMemcpy2DAsync(tmp.data(), sizeof(double2) * D.Mr, s->hs[sig].plane[w],
+                              sizeof(double2) * D.Mrp, sizeof(double2) * D.Mr, N,
+                              cudaMemcpyDeviceToHost, s->plan->stream));
+        CKR(cudaStreamSynchronize(s->plan->stream));
+        for (size_t i = 0; i < tmp.size(); ++i) host[i] = (float)tmp[i];
+        return MP_OK;
     }
     CKR(cudaMemcpy2DAsync(host, sizeof(float2) * D.Mr, s->hs[sig].plane[w], sizeof(float2) * D.Mrp,
                           sizeof(float2) * D.Mr, N, cudaMemcpyDeviceToHost, s->plan->stream));

@@ -14,32 +14,63 @@ __device__ __forceinline__ long long lmod(long long x, long long m) {
     return r < 0 ? r + m : r;
 }
 
-__device__ __forceinline__ float2 gamma_of(const DevDict& D, const float2* gam, int k) {
+// Complex element types of the coefficient planes: float2 (default) or
+// double2 (MP_COEF_FP64), with their real type and the plan's tables of
+// the same precision.
+template <typename C2> struct cx_t;
+template <> struct cx_t<float2> {
+    using R = float;
+    static __device__ __forceinline__ float2 make(float x, float y) { return make_float2(x, y); }
+    static __device__ __forceinline__ const float2* gam(const DevPlan& P) { return P.gam; }
+    static __device__ __forceinline__ const float2* tiles(const DevPlan& P) { return P.tiles; }
+    static __device__ __forceinline__ const float2* cis(const DevPlan& P) { return P.cis; }
+};
+template <> struct cx_t<double2> {
+    using R = double;
+    static __device__ __forceinline__ double2 make(double x, double y) {
+        return make_double2(x, y);
+    }
+    static __device__ __forceinline__ const double2* gam(const DevPlan& P) { return P.gam64; }
+    static __device__ __forceinline__ const double2* tiles(const DevPlan& P) { return P.tiles64; }
+    static __device__ __forceinline__ const double2* cis(const DevPlan& P) { return P.cis64; }
+};
+template <typename C2> struct plane_tables {
+    static __device__ __forceinline__ const C2* gam(const DevPlan& P) { return cx_t<C2>::gam(P); }
+};
+
+template <typename C2>
+__device__ __forceinline__ C2 gamma_of(const DevDict& D, const C2* gam, int k) {
     if (k < D.gam_lo) return gam[D.gam_off + k];
     if (k >= D.Mr - D.gam_hi) return gam[D.gam_off + D.gam_lo + (k - (D.Mr - D.gam_hi))];
-    return make_float2(0.f, 0.f);
+    return cx_t<C2>::make(0, 0);
 }
 
 // pedantic selection score (Sec. 5): energy removed by the real pair with
 // the coefficient of eq. dualatprod, eq. projenfaster; c^2 at m in {0, M/2}.
-// Non-negative, so its float bits order like the values.
-__device__ __forceinline__ float pair_score(float2 v, int m, const DevDict& D, const float2* gam) {
-    if (m == 0 || 2 * m == D.M) return v.x * v.x;
-    const float2 g = gamma_of(D, gam, m);
-    if (g.x == 0.f && g.y == 0.f) return 2.f * fmaf(v.x, v.x, v.y * v.y);
-    const float inv = 1.f / (1.f - fmaf(g.x, g.x, g.y * g.y));
-    const float cx = (v.x - fmaf(g.x, v.x, g.y * v.y)) * inv;
-    const float cy = (v.y - fmaf(g.y, v.x, -g.x * v.y)) * inv;
-    const float c2 = fmaf(cx, cx, cy * cy), d2 = fmaf(cx, cx, -cy * cy);
-    return fmaxf(0.f, 2.f * (c2 + fmaf(g.x, d2, -2.f * g.y * cx * cy)));
+// Evaluated in the planes' precision and rounded to FP32 (rounding keeps the
+// order); non-negative, so its float bits order like the values.
+template <typename C2>
+__device__ __forceinline__ float pair_score(C2 v, int m, const DevDict& D, const C2* gam) {
+    using R = typename cx_t<C2>::R;
+    if (m == 0 || 2 * m == D.M) return (float)(v.x * v.x);
+    const C2 g = gamma_of(D, gam, m);
+    if (g.x == R(0) && g.y == R(0)) return (float)(R(2) * fma(v.x, v.x, v.y * v.y));
+    const R inv = R(1) / (R(1) - fma(g.x, g.x, g.y * g.y));
+    const R cx = (v.x - fma(g.x, v.x, g.y * v.y)) * inv;
+    const R cy = (v.y - fma(g.y, v.x, -g.x * v.y)) * inv;
+    const R c2 = fma(cx, cx, cy * cy), d2 = fma(cx, cx, -cy * cy);
+    const R e = R(2) * (c2 + fma(g.x, d2, R(-2) * g.y * cx * cy));
+    return (float)(e > R(0) ? e : R(0));
 }
 
 // selection key: score bits in the high word (|rho|^2, or the pair energy
-// drop when pedantic), inverted flat index in the low word
-__device__ __forceinline__ unsigned long long make_key_sel(float2 v, unsigned flat, int m,
-                                                           const DevDict& D, const float2* gam,
+// drop when pedantic; FP32, rounded from the planes' precision), inverted
+// flat index in the low word
+template <typename C2>
+__device__ __forceinline__ unsigned long long make_key_sel(C2 v, unsigned flat, int m,
+                                                           const DevDict& D, const C2* gam,
                                                            int pedantic) {
-    const float s = pedantic ? pair_score(v, m, D, gam) : fmaf(v.x, v.x, v.y * v.y);
+    const float s = pedantic ? pair_score(v, m, D, gam) : (float)fma(v.x, v.x, v.y * v.y);
     return ((unsigned long long)__float_as_uint(s) << 32) |
            (unsigned long long)(0xffffffffu - flat);
 }

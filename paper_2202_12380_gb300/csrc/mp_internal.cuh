@@ -76,8 +76,15 @@ struct DevPlan {
     const float2* gam;
     const float* g32;
     const float2* cis;  // e^{i 2 pi q / M_w} per dictionary (FP64-rounded to FP32)
+    // MP_COEF_FP64: the same tables in FP64 (tile offsets as in `tiles`)
+    int fp64;
+    const double2* tiles64;
+    const double2* gam64;
+    const double2* cis64;
 };
 
+// Coefficient planes hold float2 entries, or double2 ones when the plan has
+// MP_COEF_FP64 (DevPlan::fp64); `plane` is then reinterpreted as double2*.
 struct DevSig {
     long long L;
     long long N[MAXW];
@@ -112,6 +119,12 @@ struct DevSig {
 // analysis: rho = A * frames for dictionary w of the listed signals
 // flagged: act only on signals whose `reanalyze` flag is set (reset pass)
 cudaError_t launch_analysis_sgemm(const float* A, int Arows, int Kp, int w_len, int a, int Mrp,
+                                  int nsig, const long long* d_tile_prefix, const DevSig* d_sigs,
+                                  int dict, long long total_frame_tiles, cudaStream_t st,
+                                  int flagged = 0);
+// FP64 analysis (MP_COEF_FP64): the same DFT-GEMM with FP64 matrix and
+// accumulation into double2 planes
+cudaError_t launch_analysis_dgemm(const double* A, int Arows, int Kp, int w_len, int a, int Mrp,
                                   int nsig, const long long* d_tile_prefix, const DevSig* d_sigs,
                                   int dict, long long total_frame_tiles, cudaStream_t st,
                                   int flagged = 0);
@@ -163,7 +176,7 @@ bool encode_bf16_map(void* map, const void* base, unsigned long long inner,
 
 size_t mp_loop_smem_bytes(const DevPlan& P, int T, int threads, int cs);
 int mp_loop_threads(int nsig, int num_sms);
-int mp_loop_max_clusters(int threads, int cs, size_t smem);
+int mp_loop_max_clusters(int threads, int cs, size_t smem, bool fp64 = false);
 
 }  // namespace mpg
 
@@ -208,6 +221,10 @@ struct mp_plan {
     float* d_g32;
     float2* d_cis32;
     float* d_A[mpg::MAXW];  // FP32 DFT matrices for the analysis, [Arows][Akp]
+    double* d_A64[mpg::MAXW];  // FP64 DFT matrices (MP_COEF_FP64), same shape
+    double2* d_tiles64;        // FP64 class tiles (MP_COEF_FP64)
+    double2* d_gam64;          // FP64 compact <d, conj d> (MP_COEF_FP64)
+    double2* d_cis64;          // FP64 modulation tables (MP_COEF_FP64)
     int Arows[mpg::MAXW], Akp[mpg::MAXW];
     // split-BF16 analysis (MP_ANALYSIS_BF16X3): A = A_hi + A_lo, [Arows][Kp64]
     void* d_Ahi[mpg::MAXW];

@@ -49,8 +49,6 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
-#include <cstdlib>
-
 #include "mp_common_dev.cuh"
 #include "mp_internal.cuh"
 
@@ -79,8 +77,9 @@ struct __align__(16) VJob {
     int pad[3];
 };
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+template <typename C2>
+__device__ __forceinline__ C2 cmul(C2 a, C2 b) {
+    return cx_t<C2>::make(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -111,11 +110,35 @@ __device__ __forceinline__ void st_async8(unsigned raddr, unsigned lo, unsigned 
         : "memory");
 }
 
+// 16-byte form (a double2 coefficient)
+__device__ __forceinline__ void st_async16(unsigned raddr, unsigned a, unsigned b, unsigned c,
+                                           unsigned d, unsigned rbar) {
+    asm volatile(
+        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, "
+        "[%5];"
+        :
+        : "r"(raddr), "r"(a), "r"(b), "r"(c), "r"(d), "r"(rbar)
+        : "memory");
+}
+
+// send the selected coefficient (float2 or double2) to CTA `lane`
+__device__ __forceinline__ void send_coef(unsigned laddr, int lane, float2 v, unsigned rbar_l) {
+    st_async8(mapa_u32(laddr, lane), __float_as_uint(v.x), __float_as_uint(v.y),
+              mapa_u32(rbar_l, lane));
+}
+__device__ __forceinline__ void send_coef(unsigned laddr, int lane, double2 v, unsigned rbar_l) {
+    const unsigned long long x = (unsigned long long)__double_as_longlong(v.x);
+    const unsigned long long y = (unsigned long long)__double_as_longlong(v.y);
+    st_async16(mapa_u32(laddr, lane), (unsigned)x, (unsigned)(x >> 32), (unsigned)y,
+               (unsigned)(y >> 32), mapa_u32(rbar_l, lane));
+}
+
 // expect this iteration's candidate bytes and the selected coefficient
-__device__ __forceinline__ void arm_exchange(unsigned xb, unsigned vb, unsigned xbytes) {
+__device__ __forceinline__ void arm_exchange(unsigned xb, unsigned vb, unsigned xbytes,
+                                             unsigned vbytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(xb), "r"(xbytes)
                  : "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(vb), "r"(8u)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(vb), "r"(vbytes)
                  : "memory");
 }
 
@@ -272,7 +295,8 @@ __device__ __forceinline__ VJob build_vjob(const DevDict* sd, const DevPair* sp,
 
 // e^{i 2 pi q / M}, q < M, from the table of dictionary D: a quarter period
 // (the quadrant k of q multiplies by i^k, exactly) or the full period
-__device__ __forceinline__ float2 cis_at(const float2* t, const DevDict& D, int q) {
+template <typename C2>
+__device__ __forceinline__ C2 cis_at(const C2* t, const DevDict& D, int q) {
     if (D.cis_q == 0) return t[q];
     int k, r;
     if (D.cis_qsh >= 0) {
@@ -282,10 +306,10 @@ __device__ __forceinline__ float2 cis_at(const float2* t, const DevDict& D, int 
         k = q / D.cis_q;
         r = q - k * D.cis_q;
     }
-    const float2 e = t[r];
-    const float x = (k & 1) ? -e.y : e.x;
-    const float y = (k & 1) ? e.x : e.y;
-    return (k & 2) ? make_float2(-x, -y) : make_float2(x, y);
+    const C2 e = t[r];
+    const auto x = (k & 1) ? -e.y : e.x;
+    const auto y = (k & 1) ? e.x : e.y;
+    return (k & 2) ? cx_t<C2>::make(-x, -y) : cx_t<C2>::make(x, y);
 }
 
 // tile column of a term for frame n: its first entry in the tile pool, or -1
@@ -299,9 +323,10 @@ __device__ __forceinline__ long long term_col(int act, int Acol, int C, int R, l
 
 // weight c e^{i 2 pi q / M_u} of column cc, q = qb + cc dq (mod M_u); zero
 // when the column misses the frame
-__device__ __forceinline__ float2 term_weight(long long tbase, int cc, int qb, int dq,
-                                              const DevDict& Du, const float2* cis_u, float2 c) {
-    if (tbase < 0) return make_float2(0.f, 0.f);
+template <typename C2>
+__device__ __forceinline__ C2 term_weight(long long tbase, int cc, int qb, int dq,
+                                          const DevDict& Du, const C2* cis_u, C2 c) {
+    if (tbase < 0) return cx_t<C2>::make(0, 0);
     int q;
     if (Du.Mmask) q = (int)(((unsigned)qb + (unsigned)cc * (unsigned)dq) & (unsigned)Du.Mmask);
     else q = (int)(((long long)qb + (long long)cc * dq) % Du.M);
@@ -310,22 +335,26 @@ __device__ __forceinline__ float2 term_weight(long long tbase, int cc, int qb, i
 
 // one frame job in registers: the frame, its level-0 keys, the columns of
 // both terms, and the loads of one batch of touched chunks
+template <typename C2>
 struct JobCtx {
     int v, n, nb;
     int cc0, cc1;
     long long tb0, tb1;
     Key l0v[MAXL0];
     int cq[CB];
-    float2 val[CB], h0[CB], h1[CB];
+    C2 val[CB], h0[CB], h1[CB];
     bool hit[CB];
 };
 
-template <int NT, bool POW2>
+// C2: element type of the coefficient planes, kernel tiles and tables --
+// float2, or double2 for MP_COEF_FP64 plans (every step then runs in FP64)
+template <int NT, bool POW2, typename C2>
 __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     k_mp_loop(DevPlan P, DevSig* __restrict__ sigs, const int* __restrict__ order,
               long long kmax, double thr_scale, long long budget_ns, int CS, int topcap,
               long long reset_it, double reset_scale) {
     namespace cg = cooperative_groups;
+    using R = typename cx_t<C2>::R;
     constexpr int NWARPS = NT / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ DevSig S;
@@ -341,8 +370,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     __shared__ Key wsel[NWARPS];    // per-warp bests of the scan
     __shared__ __align__(8) Key cand[2][16];   // CTA bests of the cluster, per parity
     __shared__ __align__(8) Key tmsg[2];       // time-limit message of CTA 0, per parity
-    __shared__ __align__(8) float2 cval[2];    // selected coefficient, per parity
-    __shared__ __align__(8) float2 scoef[2];   // adjusted coefficient, per parity
+    __shared__ __align__(16) C2 cval[2];       // selected coefficient, per parity
+    __shared__ __align__(16) C2 scoef[2];      // adjusted coefficient, per parity
     __shared__ int sbad;                       // a bounded wait gave up
     __shared__ __align__(8) unsigned long long xbar[2];  // candidate barriers, per parity
     __shared__ __align__(8) unsigned long long vbar[2];  // coefficient barriers, per parity
@@ -402,15 +431,23 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     const int gsh = sgs;
     Key* top = reinterpret_cast<Key*>(smem_raw);
     DevClass* scls = reinterpret_cast<DevClass*>(top + ((T + 1) & ~1));
-    float2* sgam = reinterpret_cast<float2*>(scls + P.ncls);
-    float2* scis = sgam + P.ngam;
+    // the tables start 16-byte aligned (offset from the shared base, so that
+    // every pointer below stays a shared-memory pointer)
+    const size_t gam_off =
+        ((size_t)(reinterpret_cast<unsigned char*>(scls + P.ncls) - smem_raw) + 15) & ~(size_t)15;
+    C2* sgam = reinterpret_cast<C2*>(smem_raw + gam_off);
+    C2* scis = sgam + P.ngam;
     unsigned* dbits = reinterpret_cast<unsigned*>(scis + P.ncis);  // dirty groups, one bit each
     unsigned short* dlist = reinterpret_cast<unsigned short*>(dbits + ((T + 31) >> 5));
     unsigned short* chl = dlist + ((T + 7) & ~7);  // touched-chunk lists
 
     for (int i = tid; i < P.ncls; i += NT) scls[i] = P.cls[i];
-    for (int i = tid; i < P.ngam; i += NT) sgam[i] = P.gam[i];
-    for (int i = tid; i < P.ncis; i += NT) scis[i] = P.cis[i];
+    {
+        const C2* pg = cx_t<C2>::gam(P);
+        const C2* pc = cx_t<C2>::cis(P);
+        for (int i = tid; i < P.ngam; i += NT) sgam[i] = pg[i];
+        for (int i = tid; i < P.ncis; i += NT) scis[i] = pc[i];
+    }
     for (int w = 0; w < W; ++w) {
         const int tb = ltb[w], te = ltb[w + 1];
         const Key* l1 = S.l1[w];
@@ -431,7 +468,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     // dictionary bases of the flat index, one per lane (lane w < W)
     const unsigned fb_l = lane < W ? S.fbase[lane] : 0xffffffffu;
     constexpr bool PREF = NT == 128;
-    const float2* __restrict__ tiles = P.tiles;
+    const C2* __restrict__ tiles = cx_t<C2>::tiles(P);
+    const C2 zero2 = cx_t<C2>::make(0, 0);
 
     // frame jobs (step 5).  job_begin: the frame n = nstart + f CS of
     // dictionary v, its level-0 keys, both terms' tile columns and the loads
@@ -439,26 +477,26 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     // coefficient).  job_end: the update (eq. fastkernupdate with the
     // modulation of eq. hkj), new chunk keys, further batches, the frame
     // maximum and the top level.
-    auto load_batch = [&](JobCtx& x, const VJob& J, int b0) {
+    auto load_batch = [&](JobCtx<C2>& x, const VJob& J, int b0) {
         const DevDict& Dv = sd[x.v];
         const int Mv = Dv.M, Mr = Dv.Mr;
         const unsigned short* lst = chl + clo[x.v];
-        const float2* prow = S.plane[x.v] + (long long)x.n * Dv.Mrp;
+        const C2* prow = reinterpret_cast<const C2*>(S.plane[x.v]) + (long long)x.n * Dv.Mrp;
         const int nb = min(CB, J.nlist - b0);  // uniform
         x.nb = nb;
         auto load_slot = [&](int q) {
             x.cq[q] = q < nb ? (int)lst[b0 + q] : -1;
             const int m = x.cq[q] * CHUNK + lane;
             const bool ok = x.cq[q] >= 0;
-            x.val[q] = ok ? prow[ok ? m : 0] : make_float2(0.f, 0.f);
+            x.val[q] = ok ? prow[ok ? m : 0] : zero2;
             int i0 = m - J.Arow0;
             i0 += i0 < 0 ? Mv : 0;
             int i1 = m - J.Arow1;
             i1 += i1 < 0 ? Mv : 0;
             const bool s0 = ok && m < Mr && x.tb0 >= 0 && i0 < J.R0;
             const bool s1 = ok && m < Mr && x.tb1 >= 0 && i1 < J.R1;
-            x.h0[q] = s0 ? __ldg(tiles + x.tb0 + i0) : make_float2(0.f, 0.f);
-            x.h1[q] = s1 ? __ldg(tiles + x.tb1 + i1) : make_float2(0.f, 0.f);
+            x.h0[q] = s0 ? __ldg(tiles + x.tb0 + i0) : zero2;
+            x.h1[q] = s1 ? __ldg(tiles + x.tb1 + i1) : zero2;
             x.hit[q] = s0 || s1;
         };
         // all loads first (one round trip), the second pair only when the
@@ -472,7 +510,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
             x.cq[2] = x.cq[3] = -1;
         }
     };
-    auto job_begin = [&](JobCtx& x, const VJob& J, int v, int f) {
+    auto job_begin = [&](JobCtx<C2>& x, const VJob& J, int v, int f) {
         const DevDict& Dv = sd[v];
         const int Nv = (int)S.N[v];
         int n = J.nstart + f * CS;
@@ -490,15 +528,15 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         x.tb1 = term_col(J.act1, J.Acol1, J.C1, J.R1, J.tile1, n, Nv, x.cc1);
         load_batch(x, J, 0);
     };
-    auto job_end = [&](JobCtx& x, const VJob& J, float2 c_main, float2 c_conj, int u) {
+    auto job_end = [&](JobCtx<C2>& x, const VJob& J, C2 c_main, C2 c_conj, int u) {
         const int v = x.v, n = x.n;
         const DevDict& Dv = sd[v];
         const int Mr = Dv.Mr, nch = Dv.nch;
-        const float2* cis_u = scis + sd[u].cis_off;
-        const float2 w0 = term_weight(x.tb0, x.cc0, J.qb0, J.dq0, sd[u], cis_u, c_main);
-        const float2 w1 = term_weight(x.tb1, x.cc1, J.qb1, J.dq1, sd[u], cis_u, c_conj);
+        const C2* cis_u = scis + sd[u].cis_off;
+        const C2 w0 = term_weight(x.tb0, x.cc0, J.qb0, J.dq0, sd[u], cis_u, c_main);
+        const C2 w1 = term_weight(x.tb1, x.cc1, J.qb1, J.dq1, sd[u], cis_u, c_conj);
         Key* l0row = S.l0[v] + (long long)n * nch;
-        float2* prow = S.plane[v] + (long long)n * Dv.Mrp;
+        C2* prow = reinterpret_cast<C2*>(S.plane[v]) + (long long)n * Dv.Mrp;
         const unsigned fn = S.fbase[v] + ((unsigned)n << Dv.msh);
         const unsigned tm = tmk[v][lane];
         Key tmax = 0ull;  // maximum of the touched chunks' new keys
@@ -506,11 +544,11 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         // update and key of one slot
         auto update_slot = [&](int q) {
             const int m = x.cq[q] * CHUNK + lane;
-            float2 x2 = x.val[q];
-            const float2 d0 = cmul(w0, x.h0[q]);
+            C2 x2 = x.val[q];
+            const C2 d0 = cmul(w0, x.h0[q]);
             x2.x -= d0.x;
             x2.y -= d0.y;
-            const float2 d1 = cmul(w1, x.h1[q]);
+            const C2 d1 = cmul(w1, x.h1[q]);
             x2.x -= d1.x;
             x2.y -= d1.y;
             if (x.hit[q]) prow[m] = x2;
@@ -623,7 +661,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                 b[0] = b[2] > b[0] ? b[2] : b[0];
                 b[1] = b[3] > b[1] ? b[3] : b[1];
                 best = warp_max_key(b[1] > b[0] ? b[1] : b[0]);
-                if (lane == 0) arm_exchange(xb, vb, xbytes);
+                if (lane == 0) arm_exchange(xb, vb, xbytes, (unsigned)sizeof(C2));
             }
         } else {
             // four independent running maxima, merged at the end
@@ -642,7 +680,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
             b0 = b2 > b0 ? b2 : b0;
             const Key r = warp_max_key(b0);
             if (lane == 0) wsel[warp] = r;
-            if (CS > 1 && tid == 0) arm_exchange(xb, vb, xbytes);
+            if (CS > 1 && tid == 0) arm_exchange(xb, vb, xbytes, (unsigned)sizeof(C2));
             __syncthreads();
             best = warp_max_key(lane < NWARPS ? wsel[lane] : 0ull);
         }
@@ -700,44 +738,45 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         // wrote it itself); in a cluster the CTA owning frame j reads it and
         // sends it to every CTA of the cluster (bytes completed on vbar),
         // while the update descriptors are built
-        float2 rho = make_float2(0.f, 0.f);
-        const float2* psel = S.plane[u] + (long long)j * sd[u].Mrp + kk;
+        C2 rho = zero2;
+        const C2* psel = reinterpret_cast<const C2*>(S.plane[u]) + (long long)j * sd[u].Mrp + kk;
         if (CS == 1) {
             if (!early || warp == NWARPS - 1) rho = *psel;
         } else if (warp == NWARPS - 1 && (j & (CS - 1)) == rank) {
-            float2 r2 = make_float2(0.f, 0.f);
+            C2 r2 = zero2;
             if (lane == 0) r2 = *psel;
-            const unsigned lo = __shfl_sync(FULL, __float_as_uint(r2.x), 0);
-            const unsigned hi = __shfl_sync(FULL, __float_as_uint(r2.y), 0);
+            r2.x = __shfl_sync(FULL, r2.x, 0);
+            r2.y = __shfl_sync(FULL, r2.y, 0);
             if (lane < CS) {
                 const unsigned laddr = (unsigned)__cvta_generic_to_shared(&cval[par]);
-                st_async8(mapa_u32(laddr, lane), lo, hi, mapa_u32(vb, lane));
+                send_coef(laddr, lane, r2, vb);
             }
         }
 
         // ---- 3. per-dictionary update descriptors; 4. real-pair adjustment --
-        // eqs. dualatprod / projenfaster: coefficient and energy drop in FP32
-        // (gamma is zero away from m = 0 and m = M/2), E accumulated in FP64
+        // eqs. dualatprod / projenfaster: coefficient and energy drop in the
+        // planes' precision (gamma is zero away from m = 0 and m = M/2), E
+        // accumulated in FP64
         // by the keeper thread, which also writes the atom and the next stop
         // decision
-        auto adjust = [&](float2 r, float& cx, float& cy) {
-            float Edf;
+        auto adjust = [&](C2 r, R& cx, R& cy) {
+            R Edf;
             if (edge) {
                 cx = r.x;
                 cy = 0.f;
                 Edf = r.x * r.x;
             } else {
-                const float2 g = gamma_of(sd[u], sgam, kk);
+                const C2 g = gamma_of(sd[u], sgam, kk);
                 if (g.x == 0.f && g.y == 0.f) {
                     cx = r.x;
                     cy = r.y;
-                    Edf = 2.f * fmaf(cx, cx, cy * cy);
+                    Edf = R(2) * fma(cx, cx, cy * cy);
                 } else {
-                    const float inv = 1.f / (1.f - fmaf(g.x, g.x, g.y * g.y));
-                    cx = (r.x - fmaf(g.x, r.x, g.y * r.y)) * inv;  // rho - conj(gamma) conj(rho)
-                    cy = (r.y - fmaf(g.y, r.x, -g.x * r.y)) * inv;
-                    const float c2 = fmaf(cx, cx, cy * cy), d2 = fmaf(cx, cx, -cy * cy);
-                    Edf = 2.f * (c2 + fmaf(g.x, d2, -2.f * g.y * cx * cy));
+                    const R inv = R(1) / (R(1) - fma(g.x, g.x, g.y * g.y));
+                    cx = (r.x - fma(g.x, r.x, g.y * r.y)) * inv;  // rho - conj(gamma) conj(rho)
+                    cy = (r.y - fma(g.y, r.x, -g.x * r.y)) * inv;
+                    const R c2 = fma(cx, cx, cy * cy), d2 = fma(cx, cx, -cy * cy);
+                    Edf = R(2) * (c2 + fma(g.x, d2, R(-2) * g.y * cx * cy));
                 }
             }
             if (tid == KEEPER) {
@@ -747,8 +786,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                     at.dict = u;
                     at.m = kk;
                     at.n = j;
-                    at.re = cx;
-                    at.im = cy;
+                    at.re = (float)cx;
+                    at.im = (float)cy;
                     S.atoms[k] = at;
                     S.errs[k] = E;
                 }
@@ -772,7 +811,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         // a warp that builds dictionary v's descriptor also issues the loads
         // of v's first owned frame (128-thread CTAs, which have the
         // registers): they fly while the barrier and the coefficient wait
-        JobCtx px;
+        JobCtx<C2> px;
         bool pref = false;
         for (int v = warp; v < W; v += NWARPS) {
             const VJob Jv = build_vjob<POW2>(sd, sp, scls, W, S, u, kk, j, edge, v, rank, CS,
@@ -783,7 +822,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                 pref = true;
             }
         }
-        float cx = 0.f, cy = 0.f;
+        R cx = R(0), cy = R(0);
         if (early && warp == NWARPS - 1) {
             bool ok = true;
             if (CS > 1) {
@@ -792,7 +831,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
             }
             adjust(rho, cx, cy);
             if (lane == 0) {
-                scoef[par] = make_float2(cx, cy);
+                scoef[par] = cx_t<C2>::make(cx, cy);
                 if (!ok) sbad = 1;
             }
         }
@@ -802,7 +841,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                 stop = -2;
                 break;
             }
-            const float2 c2 = scoef[par];
+            const C2 c2 = scoef[par];
             cx = c2.x;
             cy = c2.y;
         } else {
@@ -820,7 +859,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         // ---- 5. frame jobs: the prefetched one, then the rest dealt from one
         //         flat index (warps without a prefetched job first) ----------
         {
-            const float2 c_main = make_float2(cx, cy), c_conj = make_float2(cx, -cy);
+            const C2 c_main = cx_t<C2>::make(cx, cy), c_conj = cx_t<C2>::make(cx, -cy);
             if (pref) job_end(px, vj[px.v], c_main, c_conj, u);
             // remaining jobs per dictionary (lane w < W), inclusive prefix
             int cw = lane < W ? vj[lane].cnt : 0;
@@ -837,7 +876,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                 const int v = __popc(__ballot_sync(FULL, lane < W && g >= pre));
                 const int f = g - (v > 0 ? __shfl_sync(FULL, pre, (v + 31) & 31) : 0) +
                               __shfl_sync(FULL, off, v);
-                JobCtx x;
+                JobCtx<C2> x;
                 job_begin(x, vj[v], v, f);
                 job_end(x, vj[v], c_main, c_conj, u);
             }
@@ -912,13 +951,17 @@ int single_top(const DevSig& S, int W, int cap) {
 }
 
 // the loop instantiation for a CTA size (0 if unsupported)
-LoopKernel loop_kernel(int threads, bool pow2) {
+template <typename C2>
+LoopKernel loop_kernel_t(int threads, bool pow2) {
     switch (threads) {
-        case 512: return pow2 ? k_mp_loop<512, true> : k_mp_loop<512, false>;
-        case 256: return pow2 ? k_mp_loop<256, true> : k_mp_loop<256, false>;
-        case 128: return pow2 ? k_mp_loop<128, true> : k_mp_loop<128, false>;
+        case 512: return pow2 ? k_mp_loop<512, true, C2> : k_mp_loop<512, false, C2>;
+        case 256: return pow2 ? k_mp_loop<256, true, C2> : k_mp_loop<256, false, C2>;
+        case 128: return pow2 ? k_mp_loop<128, true, C2> : k_mp_loop<128, false, C2>;
         default: return nullptr;
     }
+}
+LoopKernel loop_kernel(int threads, bool pow2, bool fp64) {
+    return fp64 ? loop_kernel_t<double2>(threads, pow2) : loop_kernel_t<float2>(threads, pow2);
 }
 
 cudaLaunchConfig_t loop_config(int nsig, int threads, int cs, size_t smem, cudaStream_t st,
@@ -966,15 +1009,17 @@ int max_clusters(LoopKernel kf, int threads, int cs, size_t smem) {
 size_t mp_loop_smem_bytes(const DevPlan& P, int T, int, int) {
     size_t chl = 0;
     for (int w = 0; w < P.W; ++w) chl += (size_t)((P.d[w].nch + 7) & ~7);
-    size_t b = (size_t)((T + 1) & ~1) * sizeof(Key) + (size_t)P.ncls * sizeof(DevClass) +
-               (size_t)(P.ngam + P.ncis) * sizeof(float2) + 4 * (size_t)((T + 31) >> 5) +
+    const size_t c2 = P.fp64 ? sizeof(double2) : sizeof(float2);
+    size_t b = (size_t)((T + 1) & ~1) * sizeof(Key) + (size_t)P.ncls * sizeof(DevClass) + 16 +
+               (size_t)(P.ngam + P.ncis) * c2 + 4 * (size_t)((T + 31) >> 5) +
                2 * (size_t)((T + 7) & ~7) + 2 * chl;
     return (b + 15) & ~(size_t)15;
 }
 
-int mp_loop_max_clusters(int threads, int cs, size_t smem) {
-    // both instantiations have the same resources; the generic one stands in
-    return max_clusters(loop_kernel(threads, false), threads, cs, smem);
+int mp_loop_max_clusters(int threads, int cs, size_t smem, bool fp64) {
+    // the power-of-two and generic instantiations have the same resources;
+    // the generic one stands in
+    return max_clusters(loop_kernel(threads, false, fp64), threads, cs, smem);
 }
 
 int mp_loop_threads(int nsig, int num_sms) {
@@ -1002,7 +1047,7 @@ bool mp_loop_shape_ok(const DevPlan& P, const DevSig* hs, int B, int threads, in
                 tmax = t > tmax ? t : tmax;
             }
             const size_t sm = mp_loop_smem_bytes(P, tmax, threads, 1);
-            if (sm > SMEM_MAX || mp_loop_max_clusters(threads, 1, sm) < 1) continue;
+            if (sm > SMEM_MAX || mp_loop_max_clusters(threads, 1, sm, P.fp64 != 0) < 1) continue;
             out->threads = threads;
             out->cs = 1;
             out->topcap = cap;
@@ -1022,7 +1067,7 @@ bool mp_loop_shape_ok(const DevPlan& P, const DevSig* hs, int B, int threads, in
     }
     if (lt > TOPCAP_CLUSTER) return false;
     const size_t sm = mp_loop_smem_bytes(P, lt, threads, c);
-    if (sm > SMEM_MAX || mp_loop_max_clusters(threads, c, sm) < 1) return false;
+    if (sm > SMEM_MAX || mp_loop_max_clusters(threads, c, sm, P.fp64 != 0) < 1) return false;
     out->threads = threads;
     out->cs = c;
     out->topcap = TOPCAP_CLUSTER;
@@ -1034,28 +1079,19 @@ bool mp_loop_shape_ok(const DevPlan& P, const DevSig* hs, int B, int threads, in
 // are SMs to spare; they need every N_w divisible by the cluster size and the
 // per-CTA top level to fit on chip.  Otherwise one CTA per signal.
 void mp_loop_shape(const DevPlan& P, const DevSig* hs, int B, int num_sms, LoopShape* out) {
-    int nt = mp_loop_threads(B, num_sms);
+    const int nt = mp_loop_threads(B, num_sms);
     int c = B <= 8 ? 16 : B <= 16 ? 8 : B * 4 <= num_sms ? 4 : B * 2 <= num_sms ? 2 : 1;
-    int nt_override = 0;
-    if (const char* ov = getenv("MPGABOR_LOOP_THREADS")) {  // tuning overrides
-        int t = atoi(ov);
-        if (t == 128 || t == 256 || t == 512) nt_override = t;
-    }
-    if (const char* ov = getenv("MPGABOR_CLUSTER")) {
-        int t = atoi(ov);
-        if (t == 1 || t == 2 || t == 4 || t == 8 || t == 16) c = t;
-    }
     *out = LoopShape();
     // a cluster CTA runs only a few frame jobs per iteration: with up to
     // three dictionaries one warp per scheduler (and a spare warp) is fastest;
     // with more dictionaries the jobs and descriptors need more warps
     // (measured on GB300: 3 dictionaries 128 threads, 5 dictionaries 512)
-    const int nt_cluster = nt_override ? nt_override : (P.W <= 3 ? 128 : 512);
+    const int nt_cluster = P.W <= 3 ? 128 : 512;
     for (; c > 1; c >>= 1) {
         if (mp_loop_shape_ok(P, hs, B, nt_cluster, c, out)) return;
-        if (!nt_override && nt_cluster != 128 && mp_loop_shape_ok(P, hs, B, 128, c, out)) return;
+        if (nt_cluster != 128 && mp_loop_shape_ok(P, hs, B, 128, c, out)) return;
     }
-    if (mp_loop_shape_ok(P, hs, B, nt_override ? nt_override : nt, 1, out)) return;
+    if (mp_loop_shape_ok(P, hs, B, nt, 1, out)) return;
     for (int t : {512, 256, 128})
         if (mp_loop_shape_ok(P, hs, B, t, 1, out)) return;
     *out = LoopShape();
@@ -1066,7 +1102,7 @@ cudaError_t launch_mp_loop(const DevPlan& P, DevSig* d_sigs, const int* d_order,
                            const LoopShape& sh, cudaStream_t st, long long reset_it,
                            double reset_scale) {
     if (nsig <= 0) return cudaSuccess;
-    LoopKernel kf = loop_kernel(sh.threads, P.pow2 != 0);
+    LoopKernel kf = loop_kernel(sh.threads, P.pow2 != 0, P.fp64 != 0);
     if (!kf || sh.topcap < 1) return cudaErrorInvalidValue;
     cudaError_t e = prepare(kf, sh.cs, sh.smem);
     if (e != cudaSuccess) return e;

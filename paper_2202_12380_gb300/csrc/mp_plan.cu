@@ -56,6 +56,15 @@ __global__ void k_cis32(float2* cs, int n, int M) {
     cs[q] = make_float2((float)c, (float)s);
 }
 
+// the same table in FP64 (MP_COEF_FP64)
+__global__ void k_cis64(double2* cs, int n, int M) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    double s, c;
+    sincospi(2.0 * (double)q / (double)M, &s, &c);
+    cs[q] = make_double2(c, s);
+}
+
 // h[it][delta] by direct sum over the window overlap (FP64)
 __global__ void k_kernel_fp64(const double* __restrict__ gu, int wu, const double* __restrict__ gv,
                               int wv, int Mx, int an, int tmin, int ntau,
@@ -117,9 +126,14 @@ __global__ void k_class_bbox(const double2* __restrict__ h, int Mx, int an, int 
     }
 }
 
+__device__ __forceinline__ void put(float2* p, double2 v) { *p = make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ void put(double2* p, double2 v) { *p = v; }
+
+// class tile entries, FP32 (T = float2) or FP64 (T = double2)
+template <typename T>
 __global__ void k_tile_fill(const double2* __restrict__ h, int Mx, int an, int tmin, int ntau,
                             int rf, int av, int au, int cf, int ct, int i_lo, int c_lo, int R,
-                            int C, double eps, float2* __restrict__ tile) {
+                            int C, double eps, T* __restrict__ tile) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)R * C) return;
     int i = (int)(idx % R);
@@ -127,42 +141,44 @@ __global__ void k_tile_fill(const double2* __restrict__ h, int Mx, int an, int t
     long long delta = (long long)(i_lo + i) * rf - cf;
     long long tau = (long long)(c_lo + c) * av - (long long)ct * au;
     double2 v;
-    float2 o = make_float2(0.f, 0.f);
-    if (kern_at(h, Mx, an, tmin, ntau, delta, tau, eps, &v)) o = make_float2((float)v.x, (float)v.y);
-    tile[(long long)c * R + i] = o;
+    double2 o = make_double2(0.0, 0.0);
+    if (kern_at(h, Mx, an, tmin, ntau, delta, tau, eps, &v)) o = v;
+    put(tile + (long long)c * R + i, o);
 }
 
 // <d_k, conj d_k> = G((M - k, j), (k, j)) = h_{u,u}(M - 2k, 0), zero when
 // thresholded away and for k in {0, M/2} where the partner is missing.
 __global__ void k_gamma(const double2* __restrict__ h, int M, int an, int tmin, int ntau,
-                        double eps, float2* __restrict__ gam) {
+                        double eps, double2* __restrict__ gam) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k > M / 2) return;
-    float2 o = make_float2(0.f, 0.f);
+    double2 o = make_double2(0.0, 0.0);
     double2 v;
     if (k != 0 && 2 * k != M && kern_at(h, M, an, tmin, ntau, (long long)M - 2 * k, 0, eps, &v))
-        o = make_float2((float)v.x, (float)v.y);
+        o = v;
     gam[k] = o;
 }
 
 // analysis matrix: A[2m][i] = g(i) cos(2 pi m t / M), A[2m+1][i] = -g(i) sin(..),
 // t = i - w/2, m < M/2 + 1, i < w; all other entries zero.  Shape [Arows][Kp]
 // with Arows a multiple of 128 and Kp = w rounded up to 16.
+// (T = float for the FP32 analysis, double for MP_COEF_FP64)
+template <typename T>
 __global__ void k_dft_matrix(const double* __restrict__ g, int w, int Kp, int M, int Mr, int Arows,
-                             float* __restrict__ A) {
+                             T* __restrict__ A) {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)Arows * Kp) return;
     int r = (int)(idx / Kp);
     int i = (int)(idx % Kp);
     int m = r >> 1;
-    float o = 0.f;
+    double o = 0.0;
     if (m < Mr && i < w) {
         long long q = dmod((long long)m * (i - w / 2), M);
         double s, c;
         sincospi(2.0 * (double)q / (double)M, &s, &c);
-        o = (float)((r & 1) ? -g[i] * s : g[i] * c);
+        o = (r & 1) ? -g[i] * s : g[i] * c;
     }
-    A[idx] = o;
+    A[idx] = (T)o;
 }
 
 long long floordiv(long long x, long long d) {
@@ -190,8 +206,13 @@ void plan_free(mp_plan* p) {
     }
     for (int i = 0; i < MAXW * MAXW; ++i)
         if (p->d_kern[i]) cudaFree(p->d_kern[i]);
-    for (int w = 0; w < MAXW; ++w)
+    for (int w = 0; w < MAXW; ++w) {
         if (p->d_A[w]) cudaFree(p->d_A[w]);
+        if (p->d_A64[w]) cudaFree(p->d_A64[w]);
+    }
+    if (p->d_tiles64) cudaFree(p->d_tiles64);
+    if (p->d_gam64) cudaFree(p->d_gam64);
+    if (p->d_cis64) cudaFree(p->d_cis64);
     if (p->d_cls) cudaFree(p->d_cls);
     if (p->d_tiles) cudaFree(p->d_tiles);
     if (p->d_gam) cudaFree(p->d_gam);
@@ -243,10 +264,16 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
         mpg_set_error("mp_plan_create: kernel threshold must be finite and >= 0");
         return MP_EINVAL;
     }
-    if (flags & ~(unsigned)(MP_ANALYSIS_BF16X3 | MP_PEDANTIC)) {
+    if (flags & ~(unsigned)(MP_ANALYSIS_BF16X3 | MP_PEDANTIC | MP_COEF_FP64)) {
         mpg_set_error("mp_plan_create: unknown flags %u", flags);
         return MP_EINVAL;
     }
+    if ((flags & MP_ANALYSIS_BF16X3) && (flags & MP_COEF_FP64)) {
+        mpg_set_error("mp_plan_create: MP_COEF_FP64 comes with its own FP64 analysis and cannot "
+                      "be combined with MP_ANALYSIS_BF16X3");
+        return MP_EINVAL;
+    }
+    const bool fp64 = (flags & MP_COEF_FP64) != 0;
     for (int w = 0; w < W; ++w) {
         if (!windows[w] || win_len[w] <= 0 || (win_len[w] & 1) || a[w] <= 0 || M[w] <= 0 ||
             (M[w] & 1) || win_len[w] > (1 << 20) || M[w] > (1 << 16)) {
@@ -287,6 +314,10 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
     memset(p->d_A, 0, sizeof(p->d_A));
     memset(p->d_Ahi, 0, sizeof(p->d_Ahi));
     memset(p->d_Alo, 0, sizeof(p->d_Alo));
+    memset(p->d_A64, 0, sizeof(p->d_A64));
+    p->d_tiles64 = nullptr;
+    p->d_gam64 = nullptr;
+    p->d_cis64 = nullptr;
     p->d_cls = nullptr;
     p->d_tiles = nullptr;
     p->d_gam = nullptr;
@@ -351,10 +382,16 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
             }
             p->dp.ncis = tot;
             CK(cudaMalloc(&p->d_cis32, sizeof(float2) * tot));
+            if (fp64) CK(cudaMalloc(&p->d_cis64, sizeof(double2) * tot));
             for (int w = 0; w < W; ++w) {
                 const int n = p->dp.d[w].cis_q ? p->dp.d[w].cis_q : M[w];
                 k_cis32<<<(n + 255) / 256, 256, 0, st>>>(p->d_cis32 + p->dp.d[w].cis_off, n, M[w]);
                 CK(cudaGetLastError());
+                if (fp64) {
+                    k_cis64<<<(n + 255) / 256, 256, 0, st>>>(p->d_cis64 + p->dp.d[w].cis_off, n,
+                                                              M[w]);
+                    CK(cudaGetLastError());
+                }
             }
         }
         // cis tables per distinct M_max
@@ -452,6 +489,7 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
             }
         p->tiles_len = tiles_total;
         CK(cudaMalloc(&p->d_tiles, sizeof(float2) * std::max(tiles_total, 1LL)));
+        if (fp64) CK(cudaMalloc(&p->d_tiles64, sizeof(double2) * std::max(tiles_total, 1LL)));
         for (int u = 0; u < W; ++u)
             for (int v = 0; v < W; ++v) {
                 int pi = u * W + v;
@@ -466,6 +504,13 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
                             a[v], a[u], cf, ct, C.i_lo, C.c_lo, C.R, C.C, kern_thr,
                             p->d_tiles + C.off);
                         CK(cudaGetLastError());
+                        if (fp64) {
+                            k_tile_fill<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+                                p->d_kern[pi], p->Mx[pi], p->an[pi], p->tmin[pi], p->ntau[pi],
+                                PR.rf, a[v], a[u], cf, ct, C.i_lo, C.c_lo, C.R, C.C, kern_thr,
+                                p->d_tiles64 + C.off);
+                            CK(cudaGetLastError());
+                        }
                     }
             }
         CK(cudaMalloc(&p->d_cls, sizeof(DevClass) * std::max<size_t>(p->cls.size(), 1)));
@@ -474,22 +519,26 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
         // <d, conj d>: full tables, then a compact copy holding only the
         // frequencies near 0 and M/2 where it can be nonzero
         std::vector<float2> gam_compact;
+        std::vector<double2> gam_compact64;
         for (int u = 0; u < W; ++u) {
             int pi = u * W + u;
             int Mr = M[u] / 2 + 1;
-            float2* d_g = nullptr;
-            CK(cudaMalloc(&d_g, sizeof(float2) * Mr));
+            double2* d_g = nullptr;
+            CK(cudaMalloc(&d_g, sizeof(double2) * Mr));
             k_gamma<<<(Mr + 255) / 256, 256, 0, st>>>(p->d_kern[pi], M[u], p->an[pi],
                                                        p->tmin[pi], p->ntau[pi], kern_thr, d_g);
             cudaError_t e1 = cudaGetLastError();
+            std::vector<double2> hg64(Mr);
             std::vector<float2> hg(Mr);
-            cudaError_t e2 = cudaMemcpyAsync(hg.data(), d_g, sizeof(float2) * Mr,
+            cudaError_t e2 = cudaMemcpyAsync(hg64.data(), d_g, sizeof(double2) * Mr,
                                              cudaMemcpyDeviceToHost, st);
             cudaError_t e3 = cudaStreamSynchronize(st);
             cudaFree(d_g);
             CK(e1);
             CK(e2);
             CK(e3);
+            for (int k = 0; k < Mr; ++k)
+                hg[k] = make_float2((float)hg64[k].x, (float)hg64[k].y);
             p->gam_full[u].resize(2 * Mr);
             for (int k = 0; k < Mr; ++k) {
                 p->gam_full[u][2 * k] = hg[k].x;
@@ -499,20 +548,32 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
             int half = Mr / 2;
             int lo = 0, hi = 0;
             for (int k = 0; k <= half; ++k)
-                if (hg[k].x != 0.f || hg[k].y != 0.f) lo = k + 1;
+                if (hg64[k].x != 0.0 || hg64[k].y != 0.0) lo = k + 1;
             for (int k = Mr - 1; k > half; --k)
-                if (hg[k].x != 0.f || hg[k].y != 0.f) hi = std::max(hi, Mr - k);
+                if (hg64[k].x != 0.0 || hg64[k].y != 0.0) hi = std::max(hi, Mr - k);
             DevDict& D = p->dp.d[u];
             D.gam_lo = lo;
             D.gam_hi = hi;
             D.gam_off = (int)gam_compact.size();
             for (int k = 0; k < lo; ++k) gam_compact.push_back(hg[k]);
             for (int k = Mr - hi; k < Mr; ++k) gam_compact.push_back(hg[k]);
+            for (int k = 0; k < lo; ++k) gam_compact64.push_back(hg64[k]);
+            for (int k = Mr - hi; k < Mr; ++k) gam_compact64.push_back(hg64[k]);
         }
         CK(cudaMalloc(&p->d_gam, sizeof(float2) * std::max<size_t>(gam_compact.size(), 1)));
         if (!gam_compact.empty())
             CK(cudaMemcpyAsync(p->d_gam, gam_compact.data(), sizeof(float2) * gam_compact.size(),
                                cudaMemcpyHostToDevice, st));
+        if (fp64) {
+            CK(cudaMalloc(&p->d_gam64,
+                          sizeof(double2) * std::max<size_t>(gam_compact64.size(), 1)));
+            if (!gam_compact64.empty())
+                CK(cudaMemcpyAsync(p->d_gam64, gam_compact64.data(),
+                                   sizeof(double2) * gam_compact64.size(), cudaMemcpyHostToDevice,
+                                   st));
+            // the host vector is read by the copy: wait for it before it goes
+            CK(cudaStreamSynchronize(st));
+        }
         // analysis matrices
         for (int w = 0; w < W; ++w) {
             const DevDict& D = p->dp.d[w];
@@ -525,6 +586,12 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
             k_dft_matrix<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_win[w], D.wlen, kp, D.M,
                                                                        D.Mr, rows, p->d_A[w]);
             CK(cudaGetLastError());
+            if (fp64) {
+                CK(cudaMalloc(&p->d_A64[w], sizeof(double) * n));
+                k_dft_matrix<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+                    d_win[w], D.wlen, kp, D.M, D.Mr, rows, p->d_A64[w]);
+                CK(cudaGetLastError());
+            }
         }
         // split-BF16 operands and their tensor maps
         if (flags & MP_ANALYSIS_BF16X3)
@@ -550,6 +617,10 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
         p->dp.gam = p->d_gam;
         p->dp.g32 = p->d_g32;
         p->dp.cis = p->d_cis32;
+        p->dp.fp64 = fp64 ? 1 : 0;
+        p->dp.tiles64 = p->d_tiles64;
+        p->dp.gam64 = p->d_gam64;
+        p->dp.cis64 = p->d_cis64;
         p->dp.pedantic = (flags & MP_PEDANTIC) ? 1 : 0;
         p->dp.pow2 = 1;
         for (int w = 0; w < W; ++w)

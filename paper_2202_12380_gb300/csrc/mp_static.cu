@@ -2,14 +2,14 @@
 // device allocation.
 //
 // Who needs it: callers that must not call cudaMalloc while decomposing --
-// code running inside a CUDA stream capture (cudaMalloc is not a stream
-// operation and breaks the capture), real-time audio threads that may not
-// block on the allocator (cudaMalloc can synchronise the device and take
-// unbounded time), and hosts that run under a fixed device-memory budget.
-// They create the plan once at set-up (that call does allocate) and then
-// decompose with this entry point, which takes its coefficient planes, max
-// trees and bookkeeping from one file-scope device array instead of
-// allocating a state.
+// real-time audio threads that may not block on the allocator (cudaMalloc
+// can synchronise the device and take unbounded time), and hosts that run
+// under a fixed device-memory budget or have handed the device's memory to
+// their own pool allocator.  They create the plan once at set-up (that call
+// does allocate) and then decompose with this entry point, which takes its
+// coefficient planes, max trees and bookkeeping from one file-scope device
+// array instead of allocating a state.  It runs the FP32 analysis only, so
+// plans made with MP_ANALYSIS_BF16X3 are rejected.
 //
 // The array g_static_scratch (MP_STATIC_SCRATCH_BYTES) is part of the
 // library image: every GPU that loads the library holds it until the process
@@ -107,6 +107,30 @@ extern "C" int mp_decompose_static(const mp_plan* p, const float* x_dev, int64_t
         mpg_set_error("mp_decompose_static: bad argument (need plan, signal, atom buffer, "
                       "L > 0, K_max >= 1)");
         return MP_EINVAL;
+    }
+    if (p->flags & MP_COEF_FP64) {
+        mpg_set_error("mp_decompose_static: the plan asks for FP64 coefficient planes; this entry "
+                      "point holds FP32 planes only (use mp_analyze / mp_run)");
+        return MP_ENOTCOMPAT;
+    }
+    if (p->flags & MP_ANALYSIS_BF16X3) {
+        mpg_set_error("mp_decompose_static: the plan asks for the split-BF16 analysis; this entry "
+                      "point runs the FP32 analysis only (make the plan without "
+                      "MP_ANALYSIS_BF16X3, or use mp_analyze / mp_run)");
+        return MP_ENOTCOMPAT;
+    }
+    {
+        int cur = -1;
+        cudaError_t ge = cudaGetDevice(&cur);
+        if (ge != cudaSuccess) {
+            mpg_set_error("mp_decompose_static: cudaGetDevice: %s", cudaGetErrorString(ge));
+            return MP_ECUDA;
+        }
+        if (cur != p->device) {
+            mpg_set_error("mp_decompose_static: the current device is %d but the plan lives on "
+                          "device %d; make the plan's device current first", cur, p->device);
+            return MP_EINVAL;
+        }
     }
     const int W = p->W;
     int wmax = 0;

@@ -20,7 +20,7 @@ from . import build as _build
 MP_OK, MP_EINVAL, MP_ENOTCOMPAT, MP_ENOMEM, MP_ECUDA, MP_ETIMEOUT = 0, -1, -2, -3, -4, -5
 MP_STOP_NONE, MP_STOP_SNR, MP_STOP_KMAX, MP_STOP_NEGENERGY, MP_STOP_ZEROMAX, MP_STOP_INVALID = \
     0, 1, 2, 3, 4, 5
-MP_ANALYSIS_FP32, MP_ANALYSIS_BF16X3, MP_PEDANTIC = 0, 1, 2
+MP_ANALYSIS_FP32, MP_ANALYSIS_BF16X3, MP_PEDANTIC, MP_COEF_FP64 = 0, 1, 2, 4
 
 ATOM_DTYPE = np.dtype([("dict", "<i4"), ("m", "<i4"), ("n", "<i8"), ("re", "<f4"), ("im", "<f4")])
 
@@ -105,8 +105,9 @@ def _stream_handle(stream):
 class Plan:
     """Owner of an mp_plan handle plus the dictionary parameters."""
 
-    def __init__(self, handle, wins, a, M, eps, flags):
+    def __init__(self, handle, wins, a, M, eps, flags, stream=None):
         self.handle = handle
+        self.stream = _stream_handle(stream)  # cudaStream_t of the plan (None: legacy)
         self.wlen = [len(g) for g in wins]
         self.a = list(a)
         self.M = list(M)
@@ -163,7 +164,7 @@ def mp_plan_create(windows, a, M, kern_thr=1e-4, flags=MP_ANALYSIS_FP32, stream=
     h = C.c_void_p()
     _check(lib().mp_plan_create(C.byref(h), W, arr, wl, aa, MM, float(kern_thr), int(flags),
                                 _stream_handle(stream)))
-    return Plan(h, wins, a, M, kern_thr, flags)
+    return Plan(h, wins, a, M, kern_thr, flags, stream)
 
 
 def mp_plan_destroy(plan: Plan):
@@ -205,8 +206,38 @@ def mp_plan_gamma(plan: Plan, u: int):
     return buf[:, 0] + 1j * buf[:, 1]
 
 
+def _plan_stream(plan: Plan):
+    import torch
+    if plan.stream is None:
+        return torch.cuda.default_stream()
+    return torch.cuda.ExternalStream(plan.stream)
+
+
+def _wait_for_current(plan: Plan):
+    """Order the plan's stream after the work already queued on torch's
+    current stream (where the caller wrote the inputs).  No-op when the two
+    are the same stream."""
+    import torch
+    cur = torch.cuda.current_stream()
+    ps = _plan_stream(plan)
+    if ps.cuda_stream != cur.cuda_stream:
+        ps.wait_stream(cur)
+
+
+def _current_waits_for_plan(plan: Plan):
+    """Order torch's current stream after the plan's stream (where the
+    library wrote the outputs)."""
+    import torch
+    cur = torch.cuda.current_stream()
+    ps = _plan_stream(plan)
+    if ps.cuda_stream != cur.cuda_stream:
+        cur.wait_stream(ps)
+
+
 def mp_analyze(plan: Plan, xs, state: State | None = None) -> State:
-    """xs: list of float32 CUDA tensors (contiguous), one per signal."""
+    """xs: list of float32 CUDA tensors (contiguous), one per signal.  The
+    plan's stream is first ordered after torch's current stream, so inputs
+    written there are ready."""
     B = len(xs)
     lens = [int(x.numel()) for x in xs]
     for x in xs:
@@ -216,6 +247,7 @@ def mp_analyze(plan: Plan, xs, state: State | None = None) -> State:
         state = State(plan, lens)
     ptrs = (C.c_void_p * B)(*[x.data_ptr() for x in xs])
     L = (C.c_int64 * B)(*lens)
+    _wait_for_current(plan)
     _check(lib().mp_analyze(plan.handle, C.byref(state.handle), B, ptrs, L))
     return state
 
@@ -336,13 +368,21 @@ def mp_last_error() -> str:
     return lib().mp_last_error().decode(errors="replace")
 
 
-def mp_decompose_static(plan: Plan, x, K_max: int, target_snr_db: float, atoms_out, errors_out=None):
+def mp_decompose_static(plan: Plan, x, K_max: int, target_snr_db: float, atoms_out,
+                        errors_out=None, sync=True):
     """Allocation-free analysis + MP of one signal (see include/mpgabor.h).
 
     x: float32 CUDA tensor; atoms_out: CUDA tensor of at least K_max * 24
     bytes (e.g. torch.empty(K_max * 24, dtype=torch.uint8)); errors_out:
-    float64 CUDA tensor of K_max entries or None.  Returns (n_atoms, stop,
-    snr_db); the atoms are read back with atoms_from_bytes()."""
+    float64 CUDA tensor of K_max entries or None.  The plan's stream is
+    ordered after torch's current stream before the call (inputs written
+    there are ready) and torch's current stream after the plan's stream
+    afterwards (the outputs are ready for work queued there).
+    sync=True: returns (n_atoms, stop, snr_db) after synchronising the
+    plan's stream.  sync=False: passes no host outputs, so the call only
+    enqueues its work and returns None; atoms_out then holds the atoms in
+    order, and unused entries keep their previous contents.  The atoms are
+    read back with atoms_from_bytes()."""
     if not (x.is_cuda and x.is_contiguous() and str(x.dtype) == "torch.float32"):
         raise ValueError("x must be a contiguous float32 CUDA tensor")
     if atoms_out.numel() * atoms_out.element_size() < int(K_max) * ATOM_DTYPE.itemsize:
@@ -350,11 +390,14 @@ def mp_decompose_static(plan: Plan, x, K_max: int, target_snr_db: float, atoms_o
     if errors_out is not None and errors_out.numel() < int(K_max):
         raise ValueError("errors_out is too small")
     n, s, q = C.c_int64(), C.c_int(), C.c_double()
+    outs = (C.byref(n), C.byref(s), C.byref(q)) if sync else (None, None, None)
+    _wait_for_current(plan)
     _check(lib().mp_decompose_static(plan.handle, x.data_ptr(), int(x.numel()), int(K_max),
                                      float(target_snr_db), atoms_out.data_ptr(),
                                      errors_out.data_ptr() if errors_out is not None else None,
-                                     C.byref(n), C.byref(s), C.byref(q)))
-    return n.value, s.value, q.value
+                                     *outs))
+    _current_waits_for_plan(plan)
+    return (n.value, s.value, q.value) if sync else None
 
 
 def atoms_from_bytes(buf, n):

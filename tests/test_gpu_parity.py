@@ -27,9 +27,11 @@ def _plan(dicts, eps, flags=0):
     return mg.mp_plan_create(wins, [a for _, a, _ in dicts], [M for _, _, M in dicts], eps, flags)
 
 
-def _run_gpu(dicts, xs, eps, K, snr):
-    plan = _plan(dicts, eps)
+def _run_gpu(dicts, xs, eps, K, snr, shape=None, flags=0):
+    plan = _plan(dicts, eps, flags)
     st = mg.mp_analyze(plan, [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in xs])
+    if shape is not None:
+        mg.mp_state_set_launch(st, *shape)
     n, stop, q = mg.mp_run(st, K, snr)
     out = []
     for b in range(len(xs)):
@@ -281,17 +283,18 @@ def test_analyze_host_matches_device():
     assert np.array_equal(mg.mp_get_atoms(st, 0), mg.mp_get_atoms(st_h, 0))
 
 
-@pytest.mark.parametrize("cluster", ["1", "4", "16"])
+@pytest.mark.parametrize("cluster", [1, 4, 16])
 @pytest.mark.parametrize("kind", ["multi3", "mixed"])
-def test_mp_parity_launch_shapes(kind, cluster, monkeypatch):
+def test_mp_parity_launch_shapes(kind, cluster):
     """The same decomposition with one CTA per signal and with clusters of 4
     and 16 CTAs (frames interleaved across the cluster's SMs)."""
-    monkeypatch.setenv("MPGABOR_CLUSTER", cluster)
     L, dicts = _workload_small(kind)
     x = inputs.as_f32(inputs.mixture(L, 33, fs=16000.0))
     K = 300
     ref = cmp.mp_coef(dicts, x.astype(np.float64), 1e-4, K, 200.0)
-    _, _, out = _run_gpu(dicts, [x], 1e-4, K, 200.0)
+    # the default thread counts: 512 for one CTA, 128 per cluster CTA
+    threads = 512 if cluster == 1 else 128
+    _, _, out = _run_gpu(dicts, [x], 1e-4, K, 200.0, shape=(threads, cluster))
     atoms, errs, E0, stop = out[0]
     assert atoms.size == K
     compare(atoms, errs, E0, ref, min_checked=100)

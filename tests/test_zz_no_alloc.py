@@ -2,9 +2,9 @@
 mp_analyze + mp_run path.
 
 The entry point exists for callers that cannot call cudaMalloc while they
-decompose (work inside a stream capture, real-time audio threads, fixed
-device-memory budgets): its planes and trees live in a static device array
-instead of an allocated state.  Two calls in a row, on different signals,
+decompose (real-time audio threads that must not block in the allocator,
+processes held to a fixed device-memory budget): its planes and trees live
+in a static device array instead of an allocated state.  Two calls in a row, on different signals,
 must each reproduce the regular path's atoms, coefficients and energies
 (same kernels, so to within the parity tolerance and in practice exactly),
 which also shows that nothing left in the shared array by the first call
@@ -61,16 +61,65 @@ def test_static_matches_regular_two_calls():
 
 
 def test_static_without_error_buffer_and_async():
+    """No error buffer (the estimates go to the static array), and the
+    asynchronous form: no host outputs, so nothing is read back until the
+    caller synchronises.  The plan runs on its own stream while the input is
+    written on torch's current stream just before the call."""
     dicts = [(inputs.blackman(256), 64, 256)]
-    plan = mg.mp_plan_create([dicts[0][0]], [64], [256], 1e-4)
-    x = torch.from_numpy(inputs.as_f32(inputs.mixture(4096, 103, fs=16000.0))).cuda()
+    side = torch.cuda.Stream()
+    plan = mg.mp_plan_create([dicts[0][0]], [64], [256], 1e-4, stream=side)
+    xh = torch.from_numpy(inputs.as_f32(inputs.mixture(4096, 103, fs=16000.0)))
     K = 100
-    ref_atoms, _, ref_n, _, _ = _regular(plan, x, K, 200.0)
+    ref_atoms, _, ref_n, _, _ = _regular(plan, xh.cuda(), K, 200.0)
     buf = torch.empty(K * mg.ATOM_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
-    n, stop, q = mg.mp_decompose_static(plan, x, K, 200.0, buf, None)
+    n, stop, q = mg.mp_decompose_static(plan, xh.cuda(), K, 200.0, buf, None)
     assert n == ref_n == K
     atoms = mg.atoms_from_bytes(buf.cpu().numpy(), n)
     assert np.array_equal(atoms[["dict", "m", "n"]], ref_atoms[["dict", "m", "n"]])
+    buf.fill_(0xFF)
+    x = torch.empty(4096, dtype=torch.float32, device="cuda")
+    x.copy_(xh, non_blocking=True)
+    assert mg.mp_decompose_static(plan, x, K, 200.0, buf, None, sync=False) is None
+    torch.cuda.synchronize()
+    atoms = mg.atoms_from_bytes(buf.cpu().numpy(), K)
+    assert np.array_equal(atoms[["dict", "m", "n"]], ref_atoms[["dict", "m", "n"]])
+    plan.close()
+
+
+def test_static_allocates_no_device_memory():
+    """After a first call (which resolves the array's address), further calls
+    leave the device's free memory unchanged."""
+    dicts = [(inputs.blackman(w), w // 4, w) for w in (128, 256)]
+    plan = mg.mp_plan_create([d[0] for d in dicts], [d[1] for d in dicts], [d[2] for d in dicts],
+                             1e-4)
+    K = 200
+    x = torch.from_numpy(inputs.as_f32(inputs.mixture(8192, 104, fs=16000.0))).cuda()
+    buf = torch.empty(K * mg.ATOM_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    errs = torch.empty(K, dtype=torch.float64, device="cuda")
+    mg.mp_decompose_static(plan, x, K, 40.0, buf, errs)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        mg.mp_decompose_static(plan, x, K, 40.0, buf, errs)
+        mg.mp_decompose_static(plan, x, K, 40.0, buf, None, sync=False)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    plan.close()
+
+
+def test_static_rejects_split_bf16_plan():
+    """The entry point runs the FP32 analysis only; a plan asking for the
+    split-BF16 analysis is refused rather than silently analysed in FP32."""
+    dicts = [(inputs.blackman(w), w // 4, w) for w in (256, 512)]
+    plan = mg.mp_plan_create([d[0] for d in dicts], [d[1] for d in dicts], [d[2] for d in dicts],
+                             1e-4, mg.MP_ANALYSIS_BF16X3)
+    x = torch.zeros(8192, dtype=torch.float32, device="cuda")
+    buf = torch.empty(10 * mg.ATOM_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    with pytest.raises(mg.MPError) as ei:
+        mg.mp_decompose_static(plan, x, 10, 40.0, buf, None)
+    assert ei.value.code == mg.MP_ENOTCOMPAT
+    assert "BF16" in str(ei.value)
     plan.close()
 
 
