@@ -211,6 +211,65 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def _profile_l2(workload):
+    """lts__t_bytes per launch of the MP loop from the committed ncu summary,
+    or None when the kernel's code changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "mp_loop_%s.md" % workload)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"code_sha256:\s*([0-9a-f]{64})", text)
+    t = re.search(r"l2_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not (m and t):
+        return None
+    kf = os.path.join(ROOT, "paper_2202_12380_gb300", "csrc", "mp_loop.cu")
+    return float(t.group(1)) if code_sha256(kf) == m.group(1) else None
+
+
+def l2_copy_peak(torch, mbytes=24, iters=200):
+    """L2 bandwidth of a copy whose source and destination (2 x mbytes MiB)
+    stay resident in the 129 MB L2: read + write bytes / CUDA-event time,
+    best of five runs of `iters` back-to-back copies."""
+    n = (mbytes << 20) // 4
+    a = torch.randn(n, device="cuda")
+    b = torch.empty_like(a)
+    for _ in range(20):
+        b.copy_(a)
+    best = 0.0
+    for _ in range(5):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
+        for _ in range(iters):
+            b.copy_(a)
+        e[1].record()
+        torch.cuda.synchronize()
+        gbs = 2.0 * n * 4 * iters / (e[0].elapsed_time(e[1]) / 1e3) / 1e9
+        best = max(best, gbs)
+    return best
+
+
+def host_info():
+    """CPU model and logical core count of the host that runs the oracle."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"cpu_model": model, "nproc": os.cpu_count(), "machine": os.uname().machine}
+
+
 # ------------------------------------------------------------- GPU arm -----
 
 def run_gpu(args):
@@ -318,12 +377,32 @@ def run_gpu(args):
     if args.batched:
         batched = run_batched(args, mg, torch, ws, rank)
 
-    cpu = None
+    cpu, ref = None, None
     if rank == 0 and ws == 1 and args.cpu_baseline:
         g_atoms = mg.mp_get_atoms(state, 0)
         g_errs = mg.mp_get_errors(state, 0)
         g_E0 = float(g_errs[-1] * 10 ** (snrs[0] / 10)) if g_errs.size else 1.0
-        cpu = cpu_baseline(args.workload, args.cpu_atoms, g_atoms, g_errs, g_E0)
+        cpu, ref = cpu_baseline(args.workload, args.cpu_atoms, g_atoms, g_errs, g_E0)
+        if args.batched and args.cpu_batched_every > 0:
+            cpu["batched"] = cpu_baseline_batched(every=args.cpu_batched_every)
+
+    # the other workloads (one signal each): atoms/s and error against the oracle
+    secondary = []
+    if rank == 0 and args.secondary:
+        ref1 = _oracle_sample("single_gauss_16k", inputs.WORKLOADS["single_gauss_16k"]["kmax"],
+                              keep=True)[2] if args.cpu_baseline else None
+        secondary.append(run_secondary(mg, torch, "single_gauss_16k", ref=ref1, steps=3))
+        secondary.append(run_secondary(mg, torch, "multi5_2p20", flags=mg.MP_ANALYSIS_BF16X3,
+                                       label="multi5_2p20, split-BF16 analysis"))
+        secondary.append(run_secondary(mg, torch, "stress_2p23", steps=1))
+        if args.workload == "multi3_2p18":
+            secondary.append(run_secondary(mg, torch, "multi3_2p18", flags=mg.MP_COEF_FP64,
+                                           ref=ref, label="multi3_2p18, FP64 planes (parity form)"))
+
+    # L2: the loop's state of this workload is L2-resident; its bandwidth
+    # ceiling is a copy that stays in L2
+    l2_peak = l2_copy_peak(torch)
+    l2_traffic = _profile_l2(args.workload)
 
     line = {
         "metric": METRIC,
@@ -350,13 +429,19 @@ def run_gpu(args):
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": peak_src,
                      "alg_bytes_per_launch": alg_bytes,
-                     "alg_bytes_per_atom": alg_bytes / max(atoms_per_step, 1)},
+                     "alg_bytes_per_atom": alg_bytes / max(atoms_per_step, 1),
+                     "l2": {"achieved": achieved, "peak": l2_peak, "unit": "GB/s",
+                            "frac": achieved / l2_peak, "traffic": l2_traffic,
+                            "peak_source": "measured here: L2-resident copy (2 x 24 MiB), "
+                                           "read + write bytes / CUDA-event time"}},
         "clocks": clk,
         "e2e": e2e,
         "cpu_baseline": cpu,
     }
     if batched is not None:
         line["batched"] = batched
+    if secondary:
+        line["secondary"] = secondary
     if rank == 0:
         print(json.dumps(line))
     state.close()
@@ -440,6 +525,85 @@ def run_batched(args, mg, torch, ws=1, rank=0):
     return out
 
 
+def _stored_oracle_prefix(name):
+    """The oracle's first atoms of a workload as written by
+    tests/golden/make_oracle_prefix.py (None if absent)."""
+    path = os.path.join(ROOT, "tests", "golden", "%s_oracle_prefix.npz" % name)
+    if not os.path.exists(path):
+        return None
+    z = np.load(path)
+
+    class Ref:
+        pass
+
+    r = Ref()
+    for k in ("dict", "m", "n", "c", "E", "s1", "s2"):
+        setattr(r, k, z[k])
+    r.E0 = float(z["E0"])
+    r.n_atoms = int(z["dict"].size)
+    r.input_sha256 = str(z["input_sha256"])
+    return r
+
+
+def run_secondary(mg, torch, name, flags=0, steps=2, ref=None, label=None):
+    """One more workload timed like the headline (analysis + MP per step,
+    CUDA events on the plan's stream, L2 flushed between steps), with its
+    error against the oracle where one is at hand: a live oracle run (ref),
+    or the stored oracle prefix of the workload."""
+    import hashlib
+    cfg, dicts, xs = _workload(name)
+    stream = torch.cuda.Stream()
+    plan = mg.mp_plan_create([d[0] for d in dicts], [d[1] for d in dicts], [d[2] for d in dicts],
+                             cfg["eps"], flags, stream)
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    K, snr = cfg["kmax"], cfg["snr_db"]
+    state = None
+    ms = []
+    for it in range(steps + 1):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            e[0].record(stream)
+            state = mg.mp_analyze(plan, xd, state)
+            mg.mp_run_async(state, K, snr)
+            e[1].record(stream)
+        stream.synchronize()
+        if it > 0:
+            ms.append(e[0].elapsed_time(e[1]))
+    n, stops, snrs = mg.mp_get_status(state)
+    atoms = int(n.sum())
+    step = float(np.mean(ms))
+    out = {"workload": name, "label": label or name, "flags": int(flags),
+           "launch_shape": list(mg.mp_state_get_launch(state)), "atoms_per_step": atoms,
+           "ms_per_step": step, "value": atoms / (step / 1e3), "unit": UNIT,
+           "stop_reasons": [int(q) for q in stops[:4]], "final_snr_db": [float(q) for q in snrs[:4]]}
+    g_atoms = mg.mp_get_atoms(state, 0)
+    g_errs = mg.mp_get_errors(state, 0)
+    g_E0 = float(g_errs[-1] * 10 ** (snrs[0] / 10)) if g_errs.size else 1.0
+    if ref is None and name != "stress_2p23":
+        stored = _stored_oracle_prefix(name)
+        if stored is not None:
+            sha = hashlib.sha256(np.ascontiguousarray(xs[0], np.float32).tobytes()).hexdigest()
+            if sha == stored.input_sha256:
+                ref = stored
+                out["oracle"] = "stored prefix of %d atoms (tests/golden)" % stored.n_atoms
+            else:
+                out["oracle"] = "stored prefix not used: this host generated another input"
+    elif ref is not None:
+        out["oracle"] = "live oracle run of %d atoms" % ref.n_atoms
+    if ref is not None:
+        out["oracle_error"] = oracle_error(g_atoms, g_errs, g_E0, ref)
+    if name == "stress_2p23":
+        # the FP64 energy estimate against the true residual of the synthesis
+        y = torch.zeros(len(xs[0]), dtype=torch.float32, device="cuda")
+        true_snr = mg.mp_synthesize(state, 0, y)
+        out["estimate_vs_true_snr_db"] = [float(snrs[0]), float(true_snr)]
+    state.close()
+    plan.close()
+    return out
+
+
 # -------------------------------------------------------------- CPU arm -----
 
 def _oracle_sample(workload, atoms, keep=False):
@@ -452,16 +616,62 @@ def _oracle_sample(workload, atoms, keep=False):
     return (res.n_atoms, dt, res) if keep else (res.n_atoms, dt)
 
 
+def _oracle_batch_one(job):
+    """One batched-form signal decomposed by the oracle to its own stop
+    (process-pool worker)."""
+    from oracle import cmp
+    x, eps, kmax, snr = job
+    cfg, dicts, _ = _workload_dicts_only("batch256")
+    t0 = time.perf_counter()
+    res = cmp.mp_coef(dicts, x.astype(np.float64), eps, kmax, snr)
+    return res.n_atoms, time.perf_counter() - t0
+
+
+def _workload_dicts_only(name):
+    cfg = inputs.WORKLOADS[name]
+    return cfg, [(inputs.make_window(k, w), a, M) for (k, w, a, M) in cfg["dicts"]], None
+
+
+def cpu_baseline_batched(every=8, workers=None):
+    """The oracle on the batched form over all host cores: every `every`-th
+    signal of batch256 in length order, each decomposed to its own stop (30
+    dB or K = 20000) by a spawn process pool with one worker per core.
+    atoms/s = atoms of the sample / wall time of the pool."""
+    import multiprocessing as mp
+    cfg = inputs.WORKLOADS["batch256"]
+    order = np.argsort(inputs.batch_lengths(cfg, cfg["id"]), kind="stable")
+    pick = [int(i) for i in order[::every]]
+    workers = workers or os.cpu_count() or 1
+    workers = max(1, min(workers, len(pick)))
+    xs = inputs.batch_subset("batch256", pick)
+    jobs = [(x, cfg["eps"], cfg["kmax"], cfg["snr_db"]) for x in xs]
+    # longest first, so the pool's tail is short
+    jobs.sort(key=lambda j: -len(j[0]))
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(workers) as pool:
+        res = pool.map(_oracle_batch_one, jobs, chunksize=1)
+    wall = time.perf_counter() - t0
+    atoms = int(sum(r[0] for r in res))
+    return {"value": atoms / wall, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "host": host_info(),
+            "sample": "FP64 C oracle, process pool of %d workers (one signal each, 1 thread per "
+                      "worker): %d of the 256 batch256 signals (every %d-th by length, L_total "
+                      "%d) decomposed to their own stop, %d atoms in %.1f s wall" % (
+                          workers, len(pick), every, int(sum(len(j[0]) for j in jobs)), atoms,
+                          wall)}
+
+
 def cpu_baseline(workload, atoms, gpu_atoms=None, gpu_errs=None, gpu_E0=None):
     """The oracle timed on the host; with the GPU decomposition of the same
     signal also its error against the oracle over the common prefix."""
     n, dt, ref = _oracle_sample(workload, atoms, keep=True)
-    out = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    out = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_info(),
            "sample": "FP64 C oracle (coefficient-domain MP, 1 thread): analysis + first %d atoms "
                      "of the %s signal, %.1f s" % (n, workload, dt)}
     if gpu_atoms is not None:
         out["oracle_error"] = oracle_error(gpu_atoms, gpu_errs, gpu_E0, ref)
-    return out
+    return out, ref
 
 
 def oracle_error(atoms, errs, E0, ref):
@@ -489,20 +699,25 @@ def oracle_error(atoms, errs, E0, ref):
 
 
 def run_reference(args):
+    """The oracle as it stands on one host core, on the GPU arm's workload and
+    work per step: analysis + matching pursuit to the workload's own stop
+    (40 dB or K_max for multi3_2p18), so both arms time the same atoms.
+    Warm-up steps are short samples (first 1000 atoms)."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     cfg, dicts, xs = _workload(args.workload)
     for _ in range(args.warmup):
-        _oracle_sample(args.workload, max(args.ref_atoms // 10, 1))
+        _oracle_sample(args.workload, min(1000, cfg["kmax"]))
     tot_atoms, tot_t = 0, 0.0
     for _ in range(args.steps):
-        n, dt = _oracle_sample(args.workload, args.ref_atoms)
+        n, dt = _oracle_sample(args.workload, cfg["kmax"])
         tot_atoms += n
         tot_t += dt
     value = tot_atoms / tot_t
-    sample = ("FP64 C oracle (coefficient-domain MP, 1 thread): analysis + first %d atoms of the "
-              "%s signal per step" % (args.ref_atoms, args.workload))
+    sample = ("FP64 C oracle (coefficient-domain MP, 1 thread): analysis + decomposition of the "
+              "%s signal to its stop (%d atoms per step), %d steps" % (
+                  args.workload, tot_atoms // max(args.steps, 1), args.steps))
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -517,9 +732,11 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic (seeded mixture; the paper's audio is not available)",
-        "config": dict(_config_desc(args.workload, cfg, xs), parallelism="single"),
+        "config": dict(_config_desc(args.workload, cfg, xs), analysis=args.analysis,
+                       parallelism="single"),
+        "atoms_per_step": tot_atoms // max(args.steps, 1),
         "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
-                         "sample": sample},
+                         "host": host_info(), "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -545,7 +762,10 @@ def main():
                          "(0: the workload's K)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-atoms", type=int, default=50000)
-    ap.add_argument("--ref-atoms", type=int, default=10000)
+    ap.add_argument("--cpu-batched-every", type=int, default=8,
+                    help="batched CPU baseline: every n-th batch256 signal (0: skip)")
+    ap.add_argument("--no-secondary", dest="secondary", action="store_false",
+                    help="skip the single_gauss_16k / multi5_2p20 / stress_2p23 / FP64 figures")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

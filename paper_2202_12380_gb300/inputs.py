@@ -235,8 +235,17 @@ def batch_lengths(cfg, wid: int, multiple: int = 2048):
     return out
 
 
-def batch_signals(cfg, wid: int):
+def batch_signals(cfg, wid: int, indices=None):
+    """The batch's signals (all, or only those listed in `indices`; each
+    signal is the same whichever others are generated)."""
     lens = batch_lengths(cfg, wid)
     rng = np.random.default_rng(seed_for(wid, 998))
     snrs = rng.uniform(10.0, 40.0, size=len(lens))
-    return [mixture(L, seed_for(wid, i), snr_db=float(s)) for i, (L, s) in enumerate(zip(lens, snrs))]
+    idx = range(len(lens)) if indices is None else indices
+    return [mixture(lens[i], seed_for(wid, i), snr_db=float(snrs[i])) for i in idx]
+
+
+def batch_subset(name: str, indices):
+    """Float32 signals `indices` of a batched workload."""
+    cfg = WORKLOADS[name]
+    return [as_f32(x) for x in batch_signals(cfg, cfg["id"], indices)]

@@ -47,3 +47,19 @@ def test_code_hash_ignores_comments_only(tmp_path):
     open(p3, "w").write(src.replace("2 * x", "3 * x"))
     assert bench.code_sha256(p1) == bench.code_sha256(p2)
     assert bench.code_sha256(p1) != bench.code_sha256(p3)
+
+
+def test_batched_cpu_baseline_uses_a_process_pool():
+    r = bench.cpu_baseline_batched(every=128, workers=2)
+    assert r["kind"] == "oracle" and r["cores"] == 2 and r["value"] > 0
+    assert "2 of the 256 batch256 signals" in r["sample"]
+    assert r["host"]["nproc"] >= 1
+
+
+def test_stored_oracle_prefix_matches_this_host_input():
+    import hashlib
+    ref = bench._stored_oracle_prefix("multi5_2p20")
+    assert ref is not None and ref.n_atoms == 2000
+    x = inputs.workload_signal("multi5_2p20")
+    assert hashlib.sha256(np.ascontiguousarray(x, np.float32).tobytes()).hexdigest() == \
+        ref.input_sha256
