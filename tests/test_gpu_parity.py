@@ -479,3 +479,4 @@ def test_graph_replay_and_autotune():
             assert np.array_equal(mg.mp_get_atoms(st, b), direct[b])
     with pytest.raises(mg.MPError):
         mg.mp_state_set_launch(st, 96, 1)
+
