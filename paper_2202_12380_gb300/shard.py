@@ -39,3 +39,23 @@ def reduce_totals(seconds: float, atoms: float, device="cpu"):
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.all_reduce(a, op=dist.ReduceOp.SUM)
     return float(t.item()), float(a.item())
+
+
+def gather_results(mine: dict):
+    """Merge per-rank results keyed by signal index (e.g. each rank's atom
+    lists) on every rank, through torch.distributed's object gather; the
+    identity without an initialised process group.  Keys must not repeat
+    across ranks (partition() gives disjoint shards)."""
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return dict(mine)
+    parts = [None] * dist.get_world_size()
+    dist.all_gather_object(parts, dict(mine))
+    out = {}
+    for p in parts:
+        for k, v in p.items():
+            if k in out:
+                raise ValueError("signal %r was decomposed by two ranks" % (k,))
+            out[k] = v
+    return out

@@ -1,5 +1,8 @@
 """Host logic of the multi-GPU path (CPU): the length-balanced partition of
-a batch and the reduction of the totals over a world-size-2 gloo group."""
+a batch, the reduction of the totals and the gather of the per-signal
+results over a world-size-2 gloo group.  Each rank decomposes its shard
+with the FP64 oracle standing in for its GPU (no GPU on this host); the
+gathered decompositions must equal a one-process run of the whole batch."""
 import os
 import socket
 
@@ -7,7 +10,7 @@ import numpy as np
 import pytest
 
 from paper_2202_12380_gb300 import inputs
-from paper_2202_12380_gb300.shard import partition, reduce_totals
+from paper_2202_12380_gb300.shard import gather_results, partition, reduce_totals
 
 
 def test_partition_covers_each_signal_once_and_balances():
@@ -42,43 +45,62 @@ def _free_port():
     return p
 
 
-def _rank_main(rank, world, port, lens, q):
+def _batch():
+    dicts = [(inputs.blackman(w), w // 4, w) for w in (64, 128)]
+    lens = [int(x) for x in np.random.default_rng(5).integers(1, 6, 9) * 1024]
+    xs = [inputs.mixture(L, 300 + i, fs=8000.0) for i, L in enumerate(lens)]
+    return dicts, lens, xs
+
+
+def _decompose(dicts, x):
+    from oracle import cmp
+    r = cmp.mp_coef(dicts, x, 1e-4, 60, 25.0)
+    return (r.dict.tolist(), r.m.tolist(), r.n.tolist(), r.c.tolist(), r.E.tolist(), r.stop)
+
+
+def _rank_main(rank, world, port, q):
+    import time
+
     import torch.distributed as dist
 
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
+        dicts, lens, xs = _batch()
         mine = partition(lens, world)[rank]
-        # each rank "decomposes" its shard: atoms = its signals' lengths / 100,
-        # time = its load in milliseconds (stand-ins computed on the host)
-        atoms = sum(lens[i] // 100 for i in mine)
-        secs = sum(lens[i] for i in mine) / 1e6
+        t0 = time.perf_counter()
+        res = {i: _decompose(dicts, xs[i]) for i in mine}
+        secs = time.perf_counter() - t0
+        atoms = sum(len(r[0]) for r in res.values())
         t, a = reduce_totals(secs, atoms)
-        q.put((rank, mine, t, a))
+        allres = gather_results(res)
+        q.put((rank, mine, secs, t, a, allres))
     finally:
         dist.destroy_process_group()
 
 
-def test_two_rank_gloo_shards_and_totals():
+def test_two_rank_gloo_shards_totals_and_gather():
     import torch.multiprocessing as mp
 
-    lens = [int(x) for x in np.random.default_rng(5).integers(1, 50, 21) * 2048]
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, lens, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
-    got = [q.get(timeout=120) for _ in procs]
+    got = [q.get(timeout=300) for _ in procs]
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    got.sort()
+    got.sort(key=lambda g: g[0])
+    dicts, lens, xs = _batch()
     shards = [g[1] for g in got]
     assert sorted(shards[0] + shards[1]) == list(range(len(lens)))
     assert not set(shards[0]) & set(shards[1])
-    loads = [sum(lens[i] for i in s) for s in shards]
-    want_t = max(loads) / 1e6
-    want_a = sum(l // 100 for l in lens)
-    for _, _, t, a in got:
-        assert t == pytest.approx(want_t) and a == want_a
+    # one process, whole batch: the reference for the gathered results
+    ref = {i: _decompose(dicts, x) for i, x in enumerate(xs)}
+    want_atoms = sum(len(r[0]) for r in ref.values())
+    for rank, mine, secs, t, a, allres in got:
+        assert a == want_atoms                      # atoms summed over ranks
+        assert t == pytest.approx(max(g[2] for g in got))  # slowest rank's time
+        assert allres == ref                        # every signal, once, as alone
