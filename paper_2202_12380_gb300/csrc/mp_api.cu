@@ -444,6 +444,13 @@ int read_status(mp_state* s, int64_t* n_atoms, int* stop, double* snr, bool* tim
         for (int b = 0; b < s->B; ++b)
             if (dv[b].reset_pending) resets->push_back(b);
     }
+    for (int b = 0; b < s->B; ++b)
+        if (dv[b].bounds) {
+            // only a library built with MP_CHECK_BOUNDS records this
+            mpg_set_error("bounds check: signal %d, MP-loop access site %d was out of range "
+                          "(the access was skipped)", b, dv[b].bounds);
+            return MP_ECUDA;
+        }
     bool to = false;
     for (int b = 0; b < s->B; ++b) {
         if (n_atoms) n_atoms[b] = dv[b].k;

@@ -9,6 +9,24 @@ namespace mpg {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Bounds check of one access (built with -DMP_CHECK_BOUNDS, a substitute for
+// a memory sanitizer): true if 0 <= i < n; otherwise the first failing site's
+// code is recorded in *err and the caller skips the access.  Without the
+// macro it is always true and costs nothing.
+__device__ __forceinline__ bool inb(long long i, long long n, int code, int* err) {
+#ifdef MP_CHECK_BOUNDS
+    if (i >= 0 && i < n) return true;
+    atomicCAS(err, 0, code);
+    return false;
+#else
+    (void)i;
+    (void)n;
+    (void)code;
+    (void)err;
+    return true;
+#endif
+}
+
 __device__ __forceinline__ long long lmod(long long x, long long m) {
     long long r = x % m;
     return r < 0 ? r + m : r;

@@ -76,6 +76,7 @@ struct DevPlan {
     const float2* gam;
     const float* g32;
     const float2* cis;  // e^{i 2 pi q / M_w} per dictionary (FP64-rounded to FP32)
+    long long tiles_len;  // entries of the tile pool (bounds-checking build)
     // MP_COEF_FP64: the same tables in FP64 (tile offsets as in `tiles`)
     int fp64;
     const double2* tiles64;
@@ -112,7 +113,8 @@ struct DevSig {
     int reset_pending;  // the MP launch stopped for a reset
     int reanalyze;      // analysis kernels act on this signal (reset pass)
     int use_r;          // the analysis reads r instead of x
-    int pad2;
+    int bounds;         // bounds-checking build (MP_CHECK_BOUNDS): first failed
+                        // access site of the MP loop, 0 if none (always 0 otherwise)
 };
 
 // ---- host launchers implemented in the .cu files -------------------------

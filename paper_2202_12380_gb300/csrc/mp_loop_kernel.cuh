@@ -170,7 +170,8 @@ __device__ __forceinline__ VJob build_vjob(const DevDict* sd, const DevPair* sp,
                                            const DevClass* scls, int W, const DevSig& S, int u,
                                            int kk, int j, bool edge, int v, int rank, int CS,
                                            int cs_sh, int lane, VJob* out,
-                                           unsigned short* clist, unsigned char* tmk) {
+                                           unsigned short* clist, unsigned char* tmk, int ccap,
+                                           int* berr) {
     const DevDict& Du = sd[u];
     const DevDict& Dv = sd[v];
     const DevPair& PR = sp[u * W + v];
@@ -269,7 +270,8 @@ __device__ __forceinline__ VJob build_vjob(const DevDict* sd, const DevPair* sp,
         dup |= (r > 2 && c >= rl[2] && c < rh[2]);
         const bool keep = idx < total && !dup;
         const unsigned ball = __ballot_sync(FULL, keep);
-        if (keep) clist[count + __popc(ball & ((1u << lane) - 1u))] = (unsigned short)c;
+        const int pos = count + __popc(ball & ((1u << lane) - 1u));
+        if (keep && inb(pos, ccap, 1, berr)) clist[pos] = (unsigned short)c;
         count += __popc(ball);
     }
     VJob J;
@@ -385,6 +387,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     const int rank = CS > 1 ? (int)cluster.block_rank() : 0;
     const int cs_sh = __ffs(CS) - 1;
     DevSig& Sg = sigs[order[blockIdx.x / CS]];
+    int* berr = &Sg.bounds;  // bounds-checking build: first failed access site
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     {
         const int* src = reinterpret_cast<const int*>(&Sg);
@@ -458,14 +461,17 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         const int tb = ltb[w], te = ltb[w + 1];
         const Key* l1 = S.l1[w];
         if (CS > 1) {
-            for (int i = tid; i < te - tb; i += NT) top[tb + i] = l1[(long long)i * CS + rank];
+            for (int i = tid; i < te - tb; i += NT)
+                top[tb + i] = inb((long long)i * CS + rank, S.N[w], 2, berr)
+                                  ? l1[(long long)i * CS + rank] : 0ull;
         } else {
             const long long Nw = S.N[w];
             for (int i = tid; i < te - tb; i += NT) {
                 const long long f0 = (long long)i << gsh;
                 const long long f1 = min(f0 + (1ll << gsh), Nw);
                 Key m = 0ull;
-                for (long long f = f0; f < f1; ++f) m = l1[f] > m ? l1[f] : m;
+                for (long long f = f0; f < f1; ++f)
+                    if (inb(f, Nw, 3, berr)) m = l1[f] > m ? l1[f] : m;
                 top[tb + i] = m;
             }
         }
@@ -494,15 +500,16 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
             x.cq[q] = q < nb ? (int)lst[b0 + q] : -1;
             const int m = x.cq[q] * CHUNK + lane;
             const bool ok = x.cq[q] >= 0;
-            x.val[q] = ok ? prow[ok ? m : 0] : zero2;
+            const bool okm = ok && inb((long long)x.n * Dv.Mrp + m, S.N[x.v] * Dv.Mrp, 4, berr);
+            x.val[q] = okm ? prow[okm ? m : 0] : zero2;
             int i0 = m - J.Arow0;
             i0 += i0 < 0 ? Mv : 0;
             int i1 = m - J.Arow1;
             i1 += i1 < 0 ? Mv : 0;
             const bool s0 = ok && m < Mr && x.tb0 >= 0 && i0 < J.R0;
             const bool s1 = ok && m < Mr && x.tb1 >= 0 && i1 < J.R1;
-            x.h0[q] = s0 ? __ldg(tiles + x.tb0 + i0) : zero2;
-            x.h1[q] = s1 ? __ldg(tiles + x.tb1 + i1) : zero2;
+            x.h0[q] = s0 && inb(x.tb0 + i0, P.tiles_len, 5, berr) ? __ldg(tiles + x.tb0 + i0) : zero2;
+            x.h1[q] = s1 && inb(x.tb1 + i1, P.tiles_len, 6, berr) ? __ldg(tiles + x.tb1 + i1) : zero2;
             x.hit[q] = s0 || s1;
         };
         // all loads first (one round trip), the second pair only when the
@@ -528,7 +535,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
 #pragma unroll
         for (int q = 0; q < MAXL0; ++q) {
             const int c = lane + 32 * q;
-            x.l0v[q] = c < Dv.nch ? l0row[c] : 0ull;
+            x.l0v[q] = c < Dv.nch && inb((long long)n * Dv.nch + c, S.N[v] * Dv.nch, 7, berr)
+                           ? l0row[c] : 0ull;
         }
         x.tb0 = term_col(J.act0, J.Acol0, J.C0, J.R0, J.tile0, n, Nv, x.cc0);
         x.tb1 = term_col(J.act1, J.Acol1, J.C1, J.R1, J.tile1, n, Nv, x.cc1);
@@ -557,7 +565,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
             const C2 d1 = cmul(w1, x.h1[q]);
             x2.x -= d1.x;
             x2.y -= d1.y;
-            if (x.hit[q]) prow[m] = x2;
+            if (x.hit[q] && inb((long long)n * Dv.Mrp + m, S.N[v] * Dv.Mrp, 8, berr)) prow[m] = x2;
             e[q] = (x.cq[q] >= 0 && m < Mr) ? make_key_sel(x2, fn + m, m, Dv, sgam, P.pedantic)
                                             : 0ull;
         };
@@ -567,20 +575,20 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
             update_slot(0);
             update_slot(1);
             warp_max_key2(e[0], e[1]);
-            if (lane == 0) l0row[x.cq[0]] = e[0];
+            if (lane == 0 && inb(x.cq[0], nch, 9, berr)) l0row[x.cq[0]] = e[0];
             tmax = e[0] > tmax ? e[0] : tmax;
             if (nb > 1) {
-                if (lane == 1) l0row[x.cq[1]] = e[1];
+                if (lane == 1 && inb(x.cq[1], nch, 9, berr)) l0row[x.cq[1]] = e[1];
                 tmax = e[1] > tmax ? e[1] : tmax;
             }
             if (nb > 2) {
                 update_slot(2);
                 update_slot(3);
                 warp_max_key2(e[2], e[3]);
-                if (lane == 2) l0row[x.cq[2]] = e[2];
+                if (lane == 2 && inb(x.cq[2], nch, 9, berr)) l0row[x.cq[2]] = e[2];
                 tmax = e[2] > tmax ? e[2] : tmax;
                 if (nb > 3) {
-                    if (lane == 3) l0row[x.cq[3]] = e[3];
+                    if (lane == 3 && inb(x.cq[3], nch, 9, berr)) l0row[x.cq[3]] = e[3];
                     tmax = e[3] > tmax ? e[3] : tmax;
                 }
             }
@@ -597,16 +605,20 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         }
         const Key fr = warp_max_key(fb);
         if (lane == 0) {
-            S.l1[v][n] = fr;
+            if (inb(n, S.N[v], 10, berr)) S.l1[v][n] = fr;
             if (CS > 1) {
-                top[ltb[v] + (n >> cs_sh)] = fr;
+                const int ti = ltb[v] + (n >> cs_sh);
+                if (inb(ti, ltb[v + 1], 11, berr)) top[ti] = fr;
             } else if (gsh == 0) {
-                top[ltb[v] + n] = fr;
+                const int ti = ltb[v] + n;
+                if (inb(ti, ltb[v + 1], 11, berr)) top[ti] = fr;
             } else {
                 const int gi = ltb[v] + (n >> gsh);
                 const unsigned bit = 1u << (gi & 31);
-                if (!(atomicOr(&dbits[gi >> 5], bit) & bit))
-                    dlist[atomicAdd(&ndirty, 1)] = (unsigned short)gi;
+                if (inb(gi, ltb[v + 1], 12, berr) && !(atomicOr(&dbits[gi >> 5], bit) & bit)) {
+                    const int di = atomicAdd(&ndirty, 1);
+                    if (inb(di, T, 13, berr)) dlist[di] = (unsigned short)gi;
+                }
             }
         }
     };
@@ -746,11 +758,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         // while the update descriptors are built
         C2 rho = zero2;
         const C2* psel = reinterpret_cast<const C2*>(S.plane[u]) + (long long)j * sd[u].Mrp + kk;
+        const bool sel_ok = inb((long long)j * sd[u].Mrp + kk, S.N[u] * sd[u].Mrp, 14, berr) &&
+                            inb(kk, sd[u].Mr, 14, berr);
         if (CS == 1) {
-            if (!early || warp == NWARPS - 1) rho = *psel;
+            if ((!early || warp == NWARPS - 1) && sel_ok) rho = *psel;
         } else if (warp == NWARPS - 1 && (j & (CS - 1)) == rank) {
             C2 r2 = zero2;
-            if (lane == 0) r2 = *psel;
+            if (lane == 0 && sel_ok) r2 = *psel;
             r2.x = __shfl_sync(FULL, r2.x, 0);
             r2.y = __shfl_sync(FULL, r2.y, 0);
             if (lane < CS) {
@@ -787,7 +801,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
             }
             if (tid == KEEPER) {
                 E -= (double)Edf;
-                if (rank == 0) {
+                if (rank == 0 && inb(k, S.cap, 15, berr)) {
                     mp_atom at;
                     at.dict = u;
                     at.m = kk;
@@ -821,7 +835,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         bool pref = false;
         for (int v = warp; v < W; v += NWARPS) {
             const VJob Jv = build_vjob<POW2>(sd, sp, scls, W, S, u, kk, j, edge, v, rank, CS,
-                                             cs_sh, lane, &vj[v], chl + clo[v], tmk[v]);
+                                             cs_sh, lane, &vj[v], chl + clo[v], tmk[v],
+                                             clo[v + 1] - clo[v], berr);
             if (PREF && v == warp && Jv.cnt > 0) {
                 __syncwarp();  // the chunk list was written by this warp's lanes
                 job_begin(px, Jv, v, 0);
@@ -904,11 +919,12 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                 for (int f = f0; f < f1; f += 8) {
                     Key e8[8];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) e8[q] = f + q < f1 ? l1[f + q] : 0ull;
+                    for (int q = 0; q < 8; ++q)
+                        e8[q] = f + q < f1 && inb(f + q, S.N[w], 16, berr) ? l1[f + q] : 0ull;
 #pragma unroll
                     for (int q = 0; q < 8; ++q) m2 = e8[q] > m2 ? e8[q] : m2;
                 }
-                top[gi] = m2;
+                if (inb(gi, T, 17, berr)) top[gi] = m2;
                 dbits[gi >> 5] = 0u;
             }
             __syncthreads();

@@ -488,6 +488,7 @@ extern "C" int mp_plan_create(mp_plan** out, int W, const double* const* windows
                     }
             }
         p->tiles_len = tiles_total;
+        p->dp.tiles_len = tiles_total;
         CK(cudaMalloc(&p->d_tiles, sizeof(float2) * std::max(tiles_total, 1LL)));
         if (fp64) CK(cudaMalloc(&p->d_tiles64, sizeof(double2) * std::max(tiles_total, 1LL)));
         for (int u = 0; u < W; ++u)

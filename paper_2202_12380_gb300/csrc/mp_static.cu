@@ -243,6 +243,11 @@ extern "C" int mp_decompose_static(const mp_plan* p, const float* x_dev, int64_t
         DevSig out;
         CKS(cudaMemcpyAsync(&out, d_sig, sizeof(DevSig), cudaMemcpyDeviceToHost, st));
         CKS(cudaStreamSynchronize(st));
+        if (out.bounds) {
+            mpg_set_error("mp_decompose_static: bounds check: MP-loop access site %d was out of "
+                          "range (the access was skipped)", out.bounds);
+            return MP_ECUDA;
+        }
         if (n_atoms) *n_atoms = out.k;
         if (stop_reason) *stop_reason = out.stop;
         if (final_snr_db) *final_snr_db = 10.0 * std::log10(out.E0 / out.E);
