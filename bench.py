@@ -458,9 +458,12 @@ def run_gpu(args):
 
 def run_batched(args, mg, torch, ws=1, rank=0):
     """Secondary figure: the batched form (256 uneven signals, one launch),
-    launch shape picked by the autotuner, analysis + MP captured in a CUDA
-    graph and replayed.  With several ranks the 256 signals are partitioned
-    by length over the ranks (no exchange; the totals are reduced)."""
+    launch shape and launch order picked by the autotuner (the order: the
+    signals with the most atoms in the tuner's probe of this batch start
+    first), analysis + MP captured in a CUDA graph and replayed.  The loop
+    time with the default shape and order (longest signal first) is reported
+    beside it.  With several ranks the 256 signals are partitioned by length
+    over the ranks (no exchange; the totals are reduced)."""
     from paper_2202_12380_gb300 import autotune
 
     cfg, dicts, xs = _workload("batch256")
@@ -474,11 +477,28 @@ def run_batched(args, mg, torch, ws=1, rank=0):
     xd = [torch.from_numpy(x).cuda() for x in xs]
     # probe: the workload itself (its K and stop target), so the tail of the
     # long signals is part of what the tuner compares
-    shape, tune_ms = autotune.tune(plan, xd, k_probe=args.tune_atoms or cfg["kmax"],
-                                   target_snr_db=cfg["snr_db"], stream=stream, repeats=1)
+    # the loop with the default launch order (longest signal first) and the
+    # default shape, for comparison with the tuned one
     state = mg.mp_analyze(plan, xd)
+    mg.mp_run(state, cfg["kmax"], cfg["snr_db"])  # sizes the atom buffers
+    default_shape = mg.mp_state_get_launch(state)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with torch.cuda.stream(stream):
+        mg.mp_analyze(plan, xd, state)
+        e[0].record(stream)
+        mg.mp_run_async(state, cfg["kmax"], cfg["snr_db"])
+        e[1].record(stream)
+    stream.synchronize()
+    loop_default_ms = e[0].elapsed_time(e[1])
+    # autotuner: per-signal work from a probe run sets the launch order, then
+    # every feasible shape is timed with it
+    shape, tune_ms, work = autotune.tune(plan, xd, k_probe=args.tune_atoms or cfg["kmax"],
+                                         target_snr_db=cfg["snr_db"], stream=stream,
+                                         repeats=args.tune_repeats, with_work=True)
     mg.mp_state_set_launch(state, *shape)
-    mg.mp_run(state, cfg["kmax"], cfg["snr_db"])  # sizes the atom buffers before capture
+    if work is not None:
+        mg.mp_state_set_work_hint(state, work)
+    mg.mp_run(state, cfg["kmax"], cfg["snr_db"])
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream, capture_error_mode="thread_local"):
         mg.mp_analyze(plan, xd, state)
@@ -515,7 +535,11 @@ def run_batched(args, mg, torch, ws=1, rank=0):
                                "batch256")
     out = {"workload": "batch256", "analysis": args.batched_analysis, "signals": n_all,
            "L_total": L_all, "launch_shape": list(shape),
+           "launch_order": "most work first (atoms per signal from the tuner's probe of this "
+                           "batch)" if work is not None else "longest signal first",
            "autotune_ms": {"%dx%d" % k: round(v, 3) for k, v in tune_ms.items()},
+           "mp_loop_ms_default": loop_default_ms,
+           "default_launch": "%dx%d, longest signal first" % tuple(default_shape),
            "cuda_graph": True, "atoms_per_step": int(atoms_all), "ms_per_step": t_max * 1e3,
            "analysis_ms": e[0].elapsed_time(e[1]), "mp_loop_ms": loop,
            "value": atoms_all / t_max, "unit": UNIT,
@@ -765,6 +789,8 @@ def main():
     ap.add_argument("--tune-atoms", type=int, default=0,
                     help="atoms per launch-shape probe of the batched autotuner "
                          "(0: the workload's K)")
+    ap.add_argument("--tune-repeats", type=int, default=2,
+                    help="timed runs per launch shape in the autotuner (the best counts)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-atoms", type=int, default=50000)
     ap.add_argument("--cpu-batched-every", type=int, default=8,

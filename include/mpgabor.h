@@ -187,6 +187,20 @@ int mp_state_set_launch(mp_state* state, int threads, int cluster);
 int mp_state_get_launch(const mp_state* state, int* threads, int* cluster);
 
 /*
+ * Launch order of the signals (tuning, no counterpart in the paper).  With
+ * more signals than the GPU runs at once, the MP launch starts the signals
+ * in order and a CTA that finishes takes the next; by default the longer
+ * signal starts first.  work (host array of B non-negative numbers, e.g.
+ * the atoms each signal needed in an earlier run of similar signals)
+ * starts the signals with the most work first, so that the longest
+ * pursuits do not end up in the last wave; NULL restores the default.
+ * Results do not depend on the order.  Synchronises the plan's stream (call
+ * it outside a stream capture).  MP_EINVAL for a negative or non-finite
+ * entry.
+ */
+int mp_state_set_work_hint(mp_state* state, const double* work);
+
+/*
  * Resets, Alg. 2 (the paper's reset options, Sec. 7): mp_run interrupts the
  * coefficient-domain pursuit of a signal before a selection when
  * reset_every > 0 selections were made since its last reset, or when

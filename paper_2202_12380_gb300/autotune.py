@@ -9,6 +9,12 @@ dictionary set and the signal lengths.  Apply it with
 ``mpgabor.mp_state_set_launch``.  With several signals the stop target
 matters: shapes that need two waves of CTAs win or lose by how the signals'
 pursuits end, so the probe should stop the way the real run does.
+
+With several signals the tuner first runs the probe once in the default
+shape and takes each signal's atom count as its work; with that work as the
+launch order (``mpgabor.mp_state_set_work_hint``: the longest pursuits
+start first, so they do not land in the last wave) it times the shapes.
+``with_work=True`` also returns the work, for the caller's state.
 """
 from __future__ import annotations
 
@@ -37,17 +43,28 @@ def _load(path):
     return {}
 
 
-def tune(plan, xs, k_probe=2000, target_snr_db=200.0, stream=None, cache_path=None, repeats=2):
-    """Returns ((threads, cluster), {shape: ms}) for device signals xs."""
+def tune(plan, xs, k_probe=2000, target_snr_db=200.0, stream=None, cache_path=None, repeats=2,
+         order_by_work=True, with_work=False):
+    """Returns ((threads, cluster), {shape: ms}) for device signals xs, and
+    the per-signal work (atoms of the probe, None for one signal or when
+    order_by_work is off) as a third item when with_work is set."""
+    import numpy as np
     import torch
 
     sig = signature(plan, [x.numel() for x in xs])
     cache = _load(cache_path)
-    if sig in cache:
+    if sig in cache and (not with_work or "work" in cache[sig]):
         t, c = cache[sig]["shape"]
-        return (t, c), {tuple(map(int, k.split("x"))): v for k, v in cache[sig]["ms"].items()}
+        ms = {tuple(map(int, k.split("x"))): v for k, v in cache[sig]["ms"].items()}
+        return ((t, c), ms, cache[sig].get("work")) if with_work else ((t, c), ms)
     stream = stream or torch.cuda.current_stream()
     state = mg.mp_analyze(plan, xs)
+    work = None
+    if order_by_work and len(xs) > 1:
+        mg.mp_run(state, k_probe, target_snr_db)
+        n, _, _ = mg.mp_get_status(state)
+        work = [float(v) for v in np.asarray(n, dtype=np.float64)]
+        mg.mp_state_set_work_hint(state, work)
     timings = {}
     for t in THREADS:
         for c in CLUSTERS:
@@ -70,7 +87,8 @@ def tune(plan, xs, k_probe=2000, target_snr_db=200.0, stream=None, cache_path=No
     state.close()
     shape = min(timings, key=timings.get)
     if cache_path:
-        cache[sig] = {"shape": list(shape), "ms": {"%dx%d" % k: v for k, v in timings.items()}}
+        cache[sig] = {"shape": list(shape), "ms": {"%dx%d" % k: v for k, v in timings.items()},
+                      "work": work}
         os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
         json.dump(cache, open(cache_path, "w"), indent=1)
-    return shape, timings
+    return (shape, timings, work) if with_work else (shape, timings)

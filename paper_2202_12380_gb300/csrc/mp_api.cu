@@ -614,6 +614,32 @@ extern "C" int mp_state_get_launch(const mp_state* s, int* threads, int* cluster
     return MP_OK;
 }
 
+extern "C" int mp_state_set_work_hint(mp_state* s, const double* work) {
+    if (!s) {
+        mpg_set_error("mp_state_set_work_hint: null state");
+        return MP_EINVAL;
+    }
+    const int B = s->B;
+    if (work)
+        for (int b = 0; b < B; ++b)
+            if (!(work[b] >= 0.0) || !std::isfinite(work[b])) {
+                mpg_set_error("mp_state_set_work_hint: work[%d] must be finite and >= 0", b);
+                return MP_EINVAL;
+            }
+    // launch order: most work first (then the longer signal, then the lower
+    // index); without hints the longer signal first
+    std::vector<int> order(B);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        if (work && work[x] != work[y]) return work[x] > work[y];
+        return s->L[x] > s->L[y];
+    });
+    CKR(cudaMemcpyAsync(s->d_order, order.data(), sizeof(int) * B, cudaMemcpyHostToDevice,
+                        s->plan->stream));
+    CKR(cudaStreamSynchronize(s->plan->stream));
+    return MP_OK;
+}
+
 extern "C" int mp_state_set_resets(mp_state* s, int64_t reset_every, double reset_err_db) {
     if (!s || reset_every < 0 || !(reset_err_db <= 0.0)) {
         mpg_set_error("mp_state_set_resets: need reset_every >= 0 and reset_err_db <= 0");

@@ -30,6 +30,7 @@ EXPORTS = [
     "mp_state_coefficients", "mp_run", "mp_run_async", "mp_get_status", "mp_state_set_time_limit",
     "mp_get_atoms", "mp_get_errors", "mp_synthesize", "mp_state_destroy", "mp_last_error",
     "mp_decompose_static", "mp_state_set_resets", "mp_state_set_launch", "mp_state_get_launch",
+    "mp_state_set_work_hint",
 ]
 
 _lib = None
@@ -80,6 +81,7 @@ def lib():
         "mp_state_set_resets": ([vp, i64, dbl], i32),
         "mp_state_set_launch": ([vp, i32, i32], i32),
         "mp_state_get_launch": ([vp, P(i32), P(i32)], i32),
+        "mp_state_set_work_hint": ([vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -323,6 +325,18 @@ def mp_state_get_launch(state: State):
     t, c = C.c_int(), C.c_int()
     _check(lib().mp_state_get_launch(state.handle, C.byref(t), C.byref(c)))
     return t.value, c.value
+
+
+def mp_state_set_work_hint(state: State, work=None):
+    """Start the signals with the most work first (work: B non-negative
+    numbers, e.g. atoms needed in an earlier run); None: longest first."""
+    if work is None:
+        _check(lib().mp_state_set_work_hint(state.handle, None))
+        return
+    w = np.ascontiguousarray(work, dtype=np.float64)
+    if w.shape != (state.B,):
+        raise ValueError("work needs one entry per signal")
+    _check(lib().mp_state_set_work_hint(state.handle, w.ctypes.data))
 
 
 def mp_state_set_resets(state: State, reset_every: int = 0, reset_err_db: float = 0.0):

@@ -480,3 +480,27 @@ def test_graph_replay_and_autotune():
     with pytest.raises(mg.MPError):
         mg.mp_state_set_launch(st, 96, 1)
 
+
+
+def test_work_hint_changes_order_not_results():
+    """The launch order of the signals (work hints: most work first) does
+    not change any decomposition; None restores the default order."""
+    dicts = [(inputs.blackman(w), w // 4, w) for w in (128, 256, 512)]
+    lens = [4096, 16384, 8192, 2048, 12288, 6144]
+    xs = [inputs.as_f32(inputs.mixture(L, 70 + i, fs=16000.0)) for i, L in enumerate(lens)]
+    plan = _plan(dicts, 1e-4)
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    runs = []
+    for hint in (None, [1.0, 5.0, 0.0, 9.0, 2.0, 2.0], None):
+        st = mg.mp_analyze(plan, xd)
+        mg.mp_state_set_launch(st, 256, 1)
+        mg.mp_state_set_work_hint(st, hint)
+        mg.mp_run(st, 200, 30.0)
+        runs.append([mg.mp_get_atoms(st, b) for b in range(len(xs))])
+        st.close()
+    for r in runs[1:]:
+        for a, b in zip(r, runs[0]):
+            assert np.array_equal(a, b)
+    with pytest.raises(mg.MPError):
+        st = mg.mp_analyze(plan, xd)
+        mg.mp_state_set_work_hint(st, [1.0, -1.0, 0.0, 0.0, 0.0, 0.0])
