@@ -108,3 +108,32 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(mpgabor, "lib_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         mpgabor.lib()
+
+
+def test_flag_validation_is_host_side(libpath):
+    """MP_COEF_FP64 cannot be combined with the split-BF16 analysis, and
+    unknown flag bits are refused, before any device work."""
+    import numpy as np
+    lib = mpgabor.lib()
+    g = np.ascontiguousarray(np.hanning(64), np.float64)
+    arr = (ctypes.POINTER(ctypes.c_double) * 1)(g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    for flags in (mpgabor.MP_COEF_FP64 | mpgabor.MP_ANALYSIS_BF16X3, 1 << 7):
+        h = ctypes.c_void_p()
+        rc = lib.mp_plan_create(ctypes.byref(h), 1, arr, (ctypes.c_int * 1)(64),
+                                (ctypes.c_int * 1)(16), (ctypes.c_int * 1)(64), 1e-4, flags, None)
+        assert rc == mpgabor.MP_EINVAL, flags
+        assert lib.mp_last_error()
+
+
+def test_null_handles_are_refused(libpath):
+    """Calls on missing plans or states return MP_EINVAL with a message."""
+    lib = mpgabor.lib()
+    assert lib.mp_state_set_work_hint(None, None) == mpgabor.MP_EINVAL
+    assert b"null state" in lib.mp_last_error()
+    assert lib.mp_state_set_launch(None, 128, 1) == mpgabor.MP_EINVAL
+    assert lib.mp_state_set_resets(None, 1, 0.0) == mpgabor.MP_EINVAL
+    assert lib.mp_get_status(None, None, None, None) == mpgabor.MP_EINVAL
+    n = ctypes.c_int64()
+    assert lib.mp_decompose_static(None, None, 0, 0, 40.0, None, None, ctypes.byref(n), None,
+                                   None) == mpgabor.MP_EINVAL
+    assert b"bad argument" in lib.mp_last_error()
