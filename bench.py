@@ -226,6 +226,38 @@ def _profile_l2(workload):
     return float(t.group(1)) if code_sha256(kf) == m.group(1) else None
 
 
+def analysis_flops(plan, lengths):
+    """Flops of the split-BF16 analysis GEMMs: per dictionary three BF16
+    products of the [Arows x Kp] DFT matrix with the [Kp x frames] frame
+    matrix (Arows = 2 Mrp rounded up to 128 rows, Mrp = M/2 + 1 rounded up to
+    32 bins; Kp = w rounded up to 64; frames = L / a per signal)."""
+    tot = 0
+    for w, a, M in zip(plan.wlen, plan.a, plan.M):
+        mrp = 32 * -(-(M // 2 + 1) // 32)
+        arows = 128 * -(-(2 * mrp) // 128)
+        kp = 64 * -(-w // 64)
+        frames = sum(int(L) // a for L in lengths)
+        tot += 3 * 2 * arows * kp * frames
+    return tot
+
+
+def tensor_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["bf16_tflops"]), "measured (BF16 burst)"
+    return 1900.0, "fallback"
+
+
+def analysis_roofline(plan, lengths, ms):
+    flops = analysis_flops(plan, lengths)
+    peak, src = tensor_peak()
+    achieved = flops / (ms / 1e3) / 1e12
+    return {"bound": "tensor", "flops_per_launch": flops, "ms": ms, "achieved": achieved,
+            "unit": "TFLOP/s", "peak": peak, "peak_source": src, "frac": achieved / peak,
+            "time": "the whole analysis step (BF16 split of the signal, the tcgen05 GEMM of "
+                    "every dictionary, tree build, energy), CUDA events"}
+
+
 def l2_copy_peak(torch, sizes_mib=(2, 4, 8, 16, 24), iters=200):
     """L2 bandwidth of copies whose source and destination (2 x size MiB)
     stay resident in the 129 MB L2: read + write bytes / CUDA-event time,
@@ -545,6 +577,9 @@ def run_batched(args, mg, torch, ws=1, rank=0):
            "value": atoms_all / t_max, "unit": UNIT,
            "parallelism": "signals partitioned over %d ranks" % ws if ws > 1 else "single",
            "scaling": "strong" if ws > 1 else None,
+           "analysis_roofline": analysis_roofline(plan, [len(x) for x in xs],
+                                                  e[0].elapsed_time(e[1]))
+           if args.batched_analysis == "bf16x3" else None,
            "mp_loop_hbm_frac": alg / (loop / 1e3) / 1e9 / peak,
            "mp_loop_traffic": traffic,
            "mp_loop_dram_frac": (traffic / (loop / 1e3) / 1e9 / peak) if traffic else None,
@@ -600,6 +635,17 @@ def run_secondary(mg, torch, name, flags=0, steps=2, ref=None, label=None):
         stream.synchronize()
         if it > 0:
             ms.append(e[0].elapsed_time(e[1]))
+    if flags & mg.MP_ANALYSIS_BF16X3:
+        with torch.cuda.stream(stream):
+            ea = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ea[0].record(stream)
+            mg.mp_analyze(plan, xd, state)
+            ea[1].record(stream)
+            mg.mp_run_async(state, K, snr)
+        stream.synchronize()
+        ana = analysis_roofline(plan, [len(x) for x in xs], ea[0].elapsed_time(ea[1]))
+    else:
+        ana = None
     n, stops, snrs = mg.mp_get_status(state)
     atoms = int(n.sum())
     step = float(np.mean(ms))
@@ -607,6 +653,8 @@ def run_secondary(mg, torch, name, flags=0, steps=2, ref=None, label=None):
            "launch_shape": list(mg.mp_state_get_launch(state)), "atoms_per_step": atoms,
            "ms_per_step": step, "value": atoms / (step / 1e3), "unit": UNIT,
            "stop_reasons": [int(q) for q in stops[:4]], "final_snr_db": [float(q) for q in snrs[:4]]}
+    if ana is not None:
+        out["analysis_roofline"] = ana
     g_atoms = mg.mp_get_atoms(state, 0)
     g_errs = mg.mp_get_errors(state, 0)
     g_E0 = float(g_errs[-1] * 10 ** (snrs[0] / 10)) if g_errs.size else 1.0
