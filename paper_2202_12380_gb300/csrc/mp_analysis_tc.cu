@@ -14,14 +14,16 @@
 // offset q, so the B tile of frames n0 .. n0+127 is the plain box
 // rows n0 + q .. n0 + q + 127, columns r0 .. r0 + 63 of that view.
 //
-// One CTA computes a 128 (rows of A) x 128 (frames) tile: warp 0 issues TMA
-// loads into a 3-stage ring (128B-swizzled K-major tiles), one thread of
-// warp 1 issues tcgen05.mma (M=128, N=128, K=16; three products per K step)
-// into a 128-column TMEM accumulator and releases stages with
-// tcgen05.commit; all four warps then read the accumulator with tcgen05.ld
-// and write complex coefficients to the frame-major plane.  Every mbarrier
-// wait is bounded (2 s of device time); on expiry the CTA records an error,
-// waits (bounded) for its in-flight copies, frees its TMEM and returns.
+// The output is cut into 128 (rows of A) x 128 (frames) tiles, taken by a
+// persistent grid of one CTA per SM: a TMA producer thread streams the K
+// blocks of the CTA's tiles through a 3-stage ring (128B-swizzled K-major
+// tiles), an MMA thread issues tcgen05.mma (M=128, N=128, K=16; three
+// products per K step) into one of two 128-column TMEM accumulators and
+// releases stages with tcgen05.commit, and four epilogue warps read the other
+// accumulator with tcgen05.ld and write complex coefficients to the
+// frame-major plane.  Every mbarrier wait is bounded (2 s of device time); on
+// expiry the CTA records an error, waits (bounded) for its in-flight copies
+// and MMAs, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -35,7 +37,7 @@ namespace {
 constexpr int TBM = 128, TBN = 128, TBK = 64, STAGES = 3;
 constexpr int TILE_BYTES = TBM * TBK * 2;           // 16 KB per operand tile
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;         // A_hi, A_lo, B_hi, B_lo
-constexpr int TC_SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int TC_SMEM = STAGES * STAGE_BYTES + 1024 + 256;  // ring, alignment, barriers
 constexpr unsigned long long WAIT_NS = 2000000000ull;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -125,31 +127,55 @@ __device__ __forceinline__ int find_tile_sig(const long long* prefix, int nsig, 
     return lo;
 }
 
-__global__ void __launch_bounds__(128, 1)
+// Persistent form: gridDim.x CTAs (one per SM) take the 128 x 128 output
+// tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... (row tiles of one frame
+// tile consecutive, so neighbouring CTAs share the frame operand in L2).
+// Warp 4 lane 0 streams the K blocks of all its tiles through the TMA ring;
+// warp 5 lane 0 issues the MMAs of tile i into TMEM accumulator i mod 2
+// (2 x 128 columns) once the epilogue has drained it, and commits it;
+// warps 0-3 (TMEM lanes 0-127) read accumulator i mod 2 and write the plane
+// while the MMAs of tile i + 1 run.  Per tile the MMAs run in the same order
+// as one CTA per tile would, so the planes are bitwise the same.
+constexpr int TC_THREADS = 192;
+constexpr int ACC_COLS = 2 * TBN;
+
+struct TileOf {
+    int s;       // signal
+    int n0, r0;  // first frame, first row of A
+    bool skip;   // reset pass: signal not flagged
+};
+
+__device__ __forceinline__ TileOf tile_of(long long t, int nrow, const long long* tprefix, int nsig,
+                                          const DevSig* sigs, int flagged) {
+    TileOf o;
+    const long long ft = t / nrow;
+    o.r0 = (int)(t - ft * nrow) * TBM;
+    o.s = find_tile_sig(tprefix, nsig, ft);
+    o.n0 = (int)((ft - tprefix[o.s]) * TBN);
+    o.skip = flagged && !sigs[o.s].reanalyze;
+    return o;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
     k_analysis_tc(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
                   const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
                   int Kp, int a, int Mrp, int nsig, const long long* __restrict__ tprefix,
                   const int* __restrict__ brow, const DevSig* __restrict__ sigs, int dict,
-                  int* __restrict__ err, int flagged) {
+                  long long ntiles, int nrow, int* __restrict__ err, int flagged) {
     extern __shared__ unsigned char smem_raw[];
     const unsigned raw = smem_u32(smem_raw);
     const unsigned base = (raw + 1023u) & ~1023u;
     unsigned char* gbase = smem_raw + (base - raw);
-    const unsigned bar0 = base + STAGES * STAGE_BYTES;  // full[s], empty[s], done
-    const unsigned full0 = bar0, empty0 = bar0 + 8 * STAGES, done = bar0 + 16 * STAGES;
-    volatile unsigned* tmem_slot = reinterpret_cast<volatile unsigned*>(gbase + STAGES * STAGE_BYTES + 16 * STAGES + 8);
-    __shared__ int failed;
+    // barriers: full[s], empty[s], tfull[2], tempty[2], drained
+    const unsigned bar0 = base + STAGES * STAGE_BYTES;
+    const unsigned full0 = bar0, empty0 = bar0 + 8 * STAGES;
+    const unsigned tfull0 = bar0 + 16 * STAGES, tempty0 = tfull0 + 16, drained = tempty0 + 16;
+    volatile unsigned* tmem_slot =
+        reinterpret_cast<volatile unsigned*>(gbase + STAGES * STAGE_BYTES + 16 * STAGES + 40);
+    __shared__ volatile int failed;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long gt = blockIdx.x;
-    const int s = find_tile_sig(tprefix, nsig, gt);
-    const DevSig& S = sigs[s];
-    if (flagged && !S.reanalyze) return;  // uniform per CTA, before any barrier
-    const long long N = S.N[dict];
-    const int n0 = (int)((gt - tprefix[s]) * TBN);
-    const int r0 = blockIdx.y * TBM;
     const int nk = Kp / TBK;
-    const int row0 = brow[s] + n0;
 
     if (threadIdx.x == 0) {
         failed = 0;
@@ -157,14 +183,18 @@ __global__ void __launch_bounds__(128, 1)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8 * i));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0 + 8 * i));
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(done));
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tfull0 + 8 * i));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(tempty0 + 8 * i));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(drained));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32((const void*)tmem_slot)),
-                     "r"(TBN));
+                     "r"(ACC_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -172,97 +202,147 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tmem_slot;
 
-    if (warp == 0 && lane == 0) {
-        // ---- TMA producer --------------------------------------------------
-        int issued = 0;
-        for (int kb = 0; kb < nk; ++kb) {
-            const int st = kb % STAGES, round = kb / STAGES;
-            if (kb >= STAGES && !mbar_wait(empty0 + 8 * st, (round - 1) & 1, err)) {
-                failed = 1;
-                break;
+    if (warp == 4) {
+        // ---- TMA producer ------------------------------------------------
+        if (lane == 0) {
+            long long kc = 0;  // K blocks issued by this CTA
+            for (long long t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+                const TileOf T = tile_of(t, nrow, tprefix, nsig, sigs, flagged);
+                if (T.skip) continue;
+                const int row0 = brow[T.s] + T.n0;
+                for (int kb = 0; kb < nk; ++kb, ++kc) {
+                    const int st = (int)(kc % STAGES);
+                    const unsigned rnd = (unsigned)(kc / STAGES);
+                    if (kc >= STAGES && !mbar_wait(empty0 + 8 * st, (rnd - 1) & 1, err)) {
+                        failed = 1;
+                        break;
+                    }
+                    const unsigned fb = full0 + 8 * st;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                                 "r"(STAGE_BYTES)
+                                 : "memory");
+                    const unsigned sb = base + st * STAGE_BYTES;
+                    const int k0 = kb * TBK;
+                    const int q = k0 / a, rr = k0 - q * a;
+                    tma_load_2d(sb, &tAh, k0, T.r0, fb);
+                    tma_load_2d(sb + TILE_BYTES, &tAl, k0, T.r0, fb);
+                    tma_load_2d(sb + 2 * TILE_BYTES, &tBh, rr, row0 + q, fb);
+                    tma_load_2d(sb + 3 * TILE_BYTES, &tBl, rr, row0 + q, fb);
+                }
             }
-            const unsigned fb = full0 + 8 * st;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
-                         "r"(STAGE_BYTES)
-                         : "memory");
-            const unsigned sb = base + st * STAGE_BYTES;
-            const int k0 = kb * TBK;
-            const int q = k0 / a, rr = k0 - q * a;
-            tma_load_2d(sb, &tAh, k0, r0, fb);
-            tma_load_2d(sb + TILE_BYTES, &tAl, k0, r0, fb);
-            tma_load_2d(sb + 2 * TILE_BYTES, &tBh, rr, row0 + q, fb);
-            tma_load_2d(sb + 3 * TILE_BYTES, &tBl, rr, row0 + q, fb);
-            issued = kb + 1;
+            if (failed) {
+                // let the copies in flight land before the CTA can exit (bounded)
+                const long long k0 = kc > STAGES ? kc - STAGES : 0;
+                for (long long k = k0; k < kc; ++k)
+                    mbar_wait(full0 + 8 * (int)(k % STAGES), (unsigned)(k / STAGES) & 1, err);
+            }
         }
-        if (failed) {
-            // let copies in flight land before the CTA can exit (bounded)
-            for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-                mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1, err);
-        }
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp == 5) {
         // ---- MMA issuer ----------------------------------------------------
-        const unsigned idesc = idesc_bf16(TBM, TBN);
-        for (int kb = 0; kb < nk; ++kb) {
-            const int st = kb % STAGES, round = kb / STAGES;
-            if (!mbar_wait(full0 + 8 * st, round & 1, err) || failed) {
-                failed = 1;
+        if (lane == 0) {
+            const unsigned idesc = idesc_bf16(TBM, TBN);
+            long long kc = 0, tc = 0;
+            for (long long t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+                const TileOf T = tile_of(t, nrow, tprefix, nsig, sigs, flagged);
+                if (T.skip) continue;
+                const int b = (int)(tc & 1);
+                const unsigned use = (unsigned)(tc >> 1);
+                if (use >= 1 && !mbar_wait(tempty0 + 8 * b, (use - 1) & 1, err)) {
+                    failed = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned acc = tmem + (unsigned)(b * TBN);
+                for (int kb = 0; kb < nk; ++kb, ++kc) {
+                    const int st = (int)(kc % STAGES);
+                    const unsigned rnd = (unsigned)(kc / STAGES);
+                    if (!mbar_wait(full0 + 8 * st, rnd & 1, err)) {
+                        failed = 1;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const unsigned sb = base + st * STAGE_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < TBK / 16; ++kk) {
+                        const unsigned off = kk * 32;
+                        const unsigned long long ah = sw128_desc(sb + off);
+                        const unsigned long long al = sw128_desc(sb + TILE_BYTES + off);
+                        const unsigned long long bh = sw128_desc(sb + 2 * TILE_BYTES + off);
+                        const unsigned long long bl = sw128_desc(sb + 3 * TILE_BYTES + off);
+                        umma_bf16(acc, ah, bh, idesc, (kb | kk) != 0);
+                        umma_bf16(acc, ah, bl, idesc, 1);
+                        umma_bf16(acc, al, bh, idesc, 1);
+                    }
+                    umma_commit(empty0 + 8 * st);
+                }
+                if (failed) break;
+                umma_commit(tfull0 + 8 * b);
+                ++tc;
+            }
+            // every MMA this thread issued has completed before the CTA ends
+            umma_commit(drained);
+            mbar_wait(drained, 0, err);
+        }
+    } else {
+        // ---- epilogue: warps 0-3, TMEM lanes 32 w .. 32 w + 31 -------------
+        long long tc = 0;
+        for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const TileOf T = tile_of(t, nrow, tprefix, nsig, sigs, flagged);
+            if (T.skip) continue;
+            const int b = (int)(tc & 1);
+            const unsigned use = (unsigned)(tc >> 1);
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(tfull0 + 8 * b, use & 1, err) && !failed;
+            ok = __shfl_sync(FULL, ok ? 1 : 0, 0) != 0;
+            if (!ok) {
+                if (lane == 0) failed = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned sb = base + st * STAGE_BYTES;
-#pragma unroll
-            for (int kk = 0; kk < TBK / 16; ++kk) {
-                const unsigned off = kk * 32;
-                const unsigned long long ah = sw128_desc(sb + off);
-                const unsigned long long al = sw128_desc(sb + TILE_BYTES + off);
-                const unsigned long long bh = sw128_desc(sb + 2 * TILE_BYTES + off);
-                const unsigned long long bl = sw128_desc(sb + 3 * TILE_BYTES + off);
-                umma_bf16(tmem, ah, bh, idesc, (kb | kk) != 0);
-                umma_bf16(tmem, ah, bl, idesc, 1);
-                umma_bf16(tmem, al, bh, idesc, 1);
-            }
-            umma_commit(empty0 + 8 * st);
-        }
-        umma_commit(done);
-    }
-    __syncwarp();
-
-    // ---- epilogue: TMEM -> complex plane ----------------------------------
-    const bool ok = mbar_wait(done, 0, err) && !failed;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok) {
-        const int row = r0 + warp * 32 + lane;
-        const int m = row >> 1;
-        float2* plane = S.plane[dict];
+            const DevSig& S = sigs[T.s];
+            const long long N = S.N[dict];
+            const int row = T.r0 + warp * 32 + lane;
+            const int m = row >> 1;
+            float2* plane = S.plane[dict];
 #pragma unroll 1
-        for (int c0 = 0; c0 < TBN; c0 += 32) {
-            unsigned v[32];
-            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
-                "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
-                "%26, %27, %28, %29, %30, %31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                  "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                  "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
-                  "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-                  "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-                  "=r"(v[30]), "=r"(v[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            for (int c0 = 0; c0 < TBN; c0 += 32) {
+                unsigned v[32];
+                const unsigned taddr =
+                    tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(b * TBN + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, "
+                    "%9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, "
+                    "%24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                      "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                      "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+                      "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]),
+                      "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float re = __uint_as_float(v[j]);
-                const float im = __shfl_down_sync(FULL, re, 1);
-                const long long n = n0 + c0 + j;
-                if (!(lane & 1) && n < N && m < Mrp) plane[n * Mrp + m] = make_float2(re, im);
+                for (int j = 0; j < 32; ++j) {
+                    const float re = __uint_as_float(v[j]);
+                    const float im = __shfl_down_sync(FULL, re, 1);
+                    const long long n = T.n0 + c0 + j;
+                    if (!(lane & 1) && n < N && m < Mrp) plane[n * Mrp + m] = make_float2(re, im);
+                }
             }
+            // accumulator b may be overwritten now
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty0 + 8 * b)
+                             : "memory");
+            ++tc;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TBN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(ACC_COLS));
 }
 
 // hi = bf16(v), lo = bf16(v - hi), rows of length cols padded with zeros to
@@ -327,9 +407,18 @@ cudaError_t launch_analysis_tc(const void* tmaps /* 4 CUtensorMap */, int Arows,
                                          TC_SMEM);
     if (e != cudaSuccess) return e;
     const CUtensorMap* m = static_cast<const CUtensorMap*>(tmaps);
-    dim3 grid((unsigned)total_tiles, (unsigned)(Arows / TBM));
-    k_analysis_tc<<<grid, 128, TC_SMEM, st>>>(m[0], m[1], m[2], m[3], Kp, a, Mrp, nsig,
-                                              d_tile_prefix, d_brow, d_sigs, dict, d_err, flagged);
+    // one CTA per SM (the shared memory allows no second one), each looping
+    // over the tiles
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int nrow = Arows / TBM;
+    const long long ntiles = total_tiles * nrow;
+    const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
+    k_analysis_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(m[0], m[1], m[2], m[3], Kp, a, Mrp, nsig,
+                                                     d_tile_prefix, d_brow, d_sigs, dict, ntiles,
+                                                     nrow, d_err, flagged);
     return cudaGetLastError();
 }
 
