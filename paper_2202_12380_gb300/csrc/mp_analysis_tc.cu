@@ -37,7 +37,9 @@ namespace {
 constexpr int TBM = 128, TBN = 128, TBK = 64, STAGES = 3;
 constexpr int TILE_BYTES = TBM * TBK * 2;           // 16 KB per operand tile
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;         // A_hi, A_lo, B_hi, B_lo
-constexpr int TC_SMEM = STAGES * STAGE_BYTES + 1024 + 256;  // ring, alignment, barriers
+constexpr int STG_OFF = STAGES * STAGE_BYTES + 128;  // epilogue staging after ring + barriers
+constexpr int STG_BYTES = 32 * TBM * 4;               // 32 frames x 128 rows of FP32
+constexpr int TC_SMEM = STG_OFF + STG_BYTES + 1024;   // + alignment of the ring
 constexpr unsigned long long WAIT_NS = 2000000000ull;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -173,6 +175,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     volatile unsigned* tmem_slot =
         reinterpret_cast<volatile unsigned*>(gbase + STAGES * STAGE_BYTES + 16 * STAGES + 40);
     __shared__ volatile int failed;
+    __shared__ volatile int tile_ok;  // epilogue: the accumulator of this tile is ready
+    float* stg = reinterpret_cast<float*>(gbase + STG_OFF);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = Kp / TBK;
@@ -285,25 +289,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else {
         // ---- epilogue: warps 0-3, TMEM lanes 32 w .. 32 w + 31 -------------
+        // Thread 0 waits for the accumulator and shares the outcome behind a
+        // named barrier of the four warps, so they leave together on failure.
+        // Each 32-frame chunk is transposed through shared memory and written
+        // as 16-byte stores, one frame's 64 bins (512 B) per row of threads.
+        const int rl = warp * 32 + lane;
         long long tc = 0;
         for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const TileOf T = tile_of(t, nrow, tprefix, nsig, sigs, flagged);
             if (T.skip) continue;
             const int b = (int)(tc & 1);
             const unsigned use = (unsigned)(tc >> 1);
-            bool ok = true;
-            if (lane == 0) ok = mbar_wait(tfull0 + 8 * b, use & 1, err) && !failed;
-            ok = __shfl_sync(FULL, ok ? 1 : 0, 0) != 0;
-            if (!ok) {
-                if (lane == 0) failed = 1;
+            if (threadIdx.x == 0)
+                tile_ok = (mbar_wait(tfull0 + 8 * b, use & 1, err) && !failed) ? 1 : 0;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (!tile_ok) {
+                if (threadIdx.x == 0) failed = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const DevSig& S = sigs[T.s];
             const long long N = S.N[dict];
-            const int row = T.r0 + warp * 32 + lane;
-            const int m = row >> 1;
             float2* plane = S.plane[dict];
+            const int mb = T.r0 >> 1;  // first bin of the tile
 #pragma unroll 1
             for (int c0 = 0; c0 < TBN; c0 += 32) {
                 unsigned v[32];
@@ -322,12 +330,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float re = __uint_as_float(v[j]);
-                    const float im = __shfl_down_sync(FULL, re, 1);
+                for (int j = 0; j < 32; ++j) stg[j * TBM + rl] = __uint_as_float(v[j]);
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                // 32 frames x 32 float4 (two bins each): 8 per thread
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int q = threadIdx.x + 128 * i;
+                    const int j = q >> 5, p = q & 31;
                     const long long n = T.n0 + c0 + j;
-                    if (!(lane & 1) && n < N && m < Mrp) plane[n * Mrp + m] = make_float2(re, im);
+                    const int m0 = mb + 2 * p;
+                    if (n < N && m0 < Mrp)
+                        *reinterpret_cast<float4*>(plane + n * Mrp + m0) =
+                            *reinterpret_cast<const float4*>(stg + j * TBM + 4 * p);
                 }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
             }
             // accumulator b may be overwritten now
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
