@@ -159,36 +159,82 @@ __global__ void __launch_bounds__(256) k_analysis_gemm(const T* __restrict__ A, 
     }
 }
 
-// E_0 = ||x||^2 in FP64, one block per signal, fixed reduction order
-__global__ void __launch_bounds__(1024) k_energy(DevSig* sigs) {
-    DevSig& S = sigs[blockIdx.x];
-    const float* x = S.x;
-    double acc = 0.0;
-    for (long long l = threadIdx.x; l < S.L; l += blockDim.x) {
-        double v = (double)x[l];
-        acc = fma(v, v, acc);
-    }
-    __shared__ double red[32];
+// FP64 squared norms of whole signals, spread over the GPU: each signal is
+// cut into ENERGY_PARTS equal segments, one block per segment writes its
+// partial sum, and one warp per signal adds the partials; every step has a
+// fixed order, so the result does not depend on scheduling.  (The FP64 pipe
+// of this part is narrow: one block per signal took 0.58 ms for 2^20
+// samples.)
+//   RESID = false: E_0 = ||x||^2 at the start of a decomposition;
+//   RESID = true:  reset pass (Alg. 2) of the flagged signals, r = x - y and
+//                  E = E_out = ||r||^2.
+
+// sum over the block (256 threads), fixed order; valid in thread 0
+__device__ __forceinline__ double block_sum256(double acc) {
+    __shared__ double red[8];
 #pragma unroll
     for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        double v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    double v = 0.0;
+    if (threadIdx.x == 0)
 #pragma unroll
-        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-        if (threadIdx.x == 0) {
-            S.E0 = v;
-            S.E = v;
-            S.k = 0;
-            S.stop = 0;
-            S.timed_out = 0;
-            S.k_out = 0;
-            S.E_out = v;
-            S.reset_pending = 0;
-            S.reanalyze = 0;
-            S.use_r = 0;
+        for (int i = 0; i < 8; ++i) v += red[i];
+    return v;
+}
+
+template <bool RESID>
+__global__ void __launch_bounds__(256) k_sqnorm_part(DevSig* sigs, double* __restrict__ part) {
+    DevSig& S = sigs[blockIdx.y];
+    if (RESID && !S.reanalyze) return;
+    const long long per = (S.L + ENERGY_PARTS - 1) / ENERGY_PARTS;
+    const long long l0 = (long long)blockIdx.x * per;
+    const long long l1 = l0 + per < S.L ? l0 + per : S.L;
+    double acc = 0.0;
+    for (long long l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
+        double v;
+        if (RESID) {
+            const float d = S.x[l] - S.y[l];
+            S.r[l] = d;
+            v = (double)d;
+        } else {
+            v = (double)S.x[l];
         }
+        acc = fma(v, v, acc);
+    }
+    acc = block_sum256(acc);
+    if (threadIdx.x == 0) part[(size_t)blockIdx.y * ENERGY_PARTS + blockIdx.x] = acc;
+}
+
+template <bool RESID>
+__global__ void k_sqnorm_final(DevSig* sigs, int nsig, const double* __restrict__ part) {
+    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (s >= nsig) return;
+    DevSig& S = sigs[s];
+    if (RESID && !S.reanalyze) return;
+    static_assert(ENERGY_PARTS == 64, "two partials per lane");
+    double v = part[(size_t)s * ENERGY_PARTS + lane] + part[(size_t)s * ENERGY_PARTS + 32 + lane];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+    if (lane) return;
+    if (RESID) {
+        S.E = v;
+        S.E_out = v;
+        S.k_out = S.k;
+        S.reset_pending = 0;
+        S.use_r = 1;
+    } else {
+        S.E0 = v;
+        S.E = v;
+        S.k = 0;
+        S.stop = 0;
+        S.timed_out = 0;
+        S.k_out = 0;
+        S.E_out = v;
+        S.reset_pending = 0;
+        S.reanalyze = 0;
+        S.use_r = 0;
     }
 }
 
@@ -224,34 +270,6 @@ __global__ void k_tree_build(DevPlan P, const DevSig* __restrict__ sigs, int nsi
 
 // reset pass, one block per signal: r = x - y and E = E_out = ||r||^2
 // (FP64, fixed order) for the flagged signals
-__global__ void __launch_bounds__(1024) k_reset_residual(DevSig* sigs) {
-    DevSig& S = sigs[blockIdx.x];
-    if (!S.reanalyze) return;
-    double acc = 0.0;
-    for (long long l = threadIdx.x; l < S.L; l += blockDim.x) {
-        const float d = S.x[l] - S.y[l];
-        S.r[l] = d;
-        acc = fma((double)d, (double)d, acc);
-    }
-    __shared__ double red[32];
-#pragma unroll
-    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-        if (threadIdx.x == 0) {
-            S.E = v;
-            S.E_out = v;
-            S.k_out = S.k;
-            S.reset_pending = 0;
-            S.use_r = 1;
-        }
-    }
-}
-
 }  // namespace
 
 cudaError_t launch_analysis_sgemm(const float* A, int Arows, int Kp, int w_len, int a, int Mrp,
@@ -276,14 +294,22 @@ cudaError_t launch_analysis_dgemm(const double* A, int Arows, int Kp, int w_len,
     return cudaGetLastError();
 }
 
-cudaError_t launch_reset_residual(DevSig* d_sigs, int nsig, cudaStream_t st) {
-    k_reset_residual<<<nsig, 1024, 0, st>>>(d_sigs);
+template <bool RESID>
+static cudaError_t launch_sqnorm(DevSig* d_sigs, int nsig, double* d_part, cudaStream_t st) {
+    if (nsig <= 0) return cudaSuccess;
+    k_sqnorm_part<RESID><<<dim3(ENERGY_PARTS, (unsigned)nsig), 256, 0, st>>>(d_sigs, d_part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sqnorm_final<RESID><<<(unsigned)((nsig + 7) / 8), 256, 0, st>>>(d_sigs, nsig, d_part);
     return cudaGetLastError();
 }
 
-cudaError_t launch_energy(const DevSig* d_sigs, int nsig, double*, int, cudaStream_t st) {
-    k_energy<<<nsig, 1024, 0, st>>>(const_cast<DevSig*>(d_sigs));
-    return cudaGetLastError();
+cudaError_t launch_reset_residual(DevSig* d_sigs, int nsig, double* d_part, cudaStream_t st) {
+    return launch_sqnorm<true>(d_sigs, nsig, d_part, st);
+}
+
+cudaError_t launch_energy(DevSig* d_sigs, int nsig, double* d_part, cudaStream_t st) {
+    return launch_sqnorm<false>(d_sigs, nsig, d_part, st);
 }
 
 cudaError_t launch_tree_build(const DevPlan& P, const DevSig* d_sigs, int nsig,

@@ -14,14 +14,17 @@
 // offset q, so the B tile of frames n0 .. n0+127 is the plain box
 // rows n0 + q .. n0 + q + 127, columns r0 .. r0 + 63 of that view.
 //
-// The output is cut into 128 (rows of A) x 128 (frames) tiles, taken by a
-// persistent grid of one CTA per SM: a TMA producer thread streams the K
-// blocks of the CTA's tiles through a 3-stage ring (128B-swizzled K-major
-// tiles), an MMA thread issues tcgen05.mma (M=128, N=128, K=16; three
-// products per K step) into one of two 128-column TMEM accumulators and
-// releases stages with tcgen05.commit, and four epilogue warps read the other
-// accumulator with tcgen05.ld and write complex coefficients to the
-// frame-major plane.  Every mbarrier wait is bounded (2 s of device time); on
+// The output is cut into 128 (rows of A) x BN (frames) tiles, BN = 128 or
+// 256, taken by a persistent grid of one CTA per SM: a TMA producer thread
+// streams the K blocks of the CTA's tiles through a ring of 3 (BN = 128) or
+// 2 (BN = 256) stages of 128B-swizzled K-major tiles, an MMA thread issues
+// tcgen05.mma (M=128, N=BN, K=16; three products per K step) into one of two
+// BN-column TMEM accumulators and releases stages with tcgen05.commit, and
+// four epilogue warps read the other accumulator with tcgen05.ld and write
+// complex coefficients to the frame-major plane.  A 256-frame tile loads
+// 96 KB of operands per K block for twice the products of a 128-frame tile
+// (64 KB), so the operand traffic per flop falls by a quarter; the host takes
+// it when there are many tiles (batches), where the loads set the pace.  Every mbarrier wait is bounded (2 s of device time); on
 // expiry the CTA records an error, waits (bounded) for its in-flight copies
 // and MMAs, frees its TMEM and returns.
 #include <cuda.h>
@@ -34,12 +37,23 @@
 namespace mpg {
 namespace {
 
-constexpr int TBM = 128, TBN = 128, TBK = 64, STAGES = 3;
-constexpr int TILE_BYTES = TBM * TBK * 2;           // 16 KB per operand tile
-constexpr int STAGE_BYTES = 4 * TILE_BYTES;         // A_hi, A_lo, B_hi, B_lo
-constexpr int STG_OFF = STAGES * STAGE_BYTES + 128;  // epilogue staging after ring + barriers
-constexpr int STG_BYTES = 32 * TBM * 4;               // 32 frames x 128 rows of FP32
-constexpr int TC_SMEM = STG_OFF + STG_BYTES + 1024;   // + alignment of the ring
+constexpr int TBM = 128, TBK = 64;
+constexpr int TILE_BYTES = TBM * TBK * 2;  // 16 KB: one A operand tile (128 rows)
+constexpr int STG_BYTES = 32 * TBM * 4;    // epilogue staging: 32 frames x 128 rows of FP32
+
+// shared-memory layout of the BN-frame form: the ring (A_hi, A_lo, B_hi,
+// B_lo per stage), 128 bytes of barriers, the epilogue staging, and 1024
+// bytes for the alignment of the ring
+template <int BN>
+struct TcCfg {
+    static constexpr int STAGES = BN == 256 ? 2 : 3;
+    static constexpr int B_BYTES = BN * TBK * 2;
+    static constexpr int STAGE_BYTES = 2 * TILE_BYTES + 2 * B_BYTES;
+    static constexpr int STG_OFF = STAGES * STAGE_BYTES + 128;
+    static constexpr int SMEM = STG_OFF + STG_BYTES + 1024;
+    static constexpr int ACC_COLS = 2 * BN;  // two accumulators
+};
+static_assert(TcCfg<256>::SMEM <= 227 * 1024, "256-frame ring exceeds shared memory");
 constexpr unsigned long long WAIT_NS = 2000000000ull;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -129,17 +143,16 @@ __device__ __forceinline__ int find_tile_sig(const long long* prefix, int nsig, 
     return lo;
 }
 
-// Persistent form: gridDim.x CTAs (one per SM) take the 128 x 128 output
+// Persistent form: gridDim.x CTAs (one per SM) take the 128 x BN output
 // tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... (row tiles of one frame
 // tile consecutive, so neighbouring CTAs share the frame operand in L2).
 // Warp 4 lane 0 streams the K blocks of all its tiles through the TMA ring;
 // warp 5 lane 0 issues the MMAs of tile i into TMEM accumulator i mod 2
-// (2 x 128 columns) once the epilogue has drained it, and commits it;
+// (2 x BN columns) once the epilogue has drained it, and commits it;
 // warps 0-3 (TMEM lanes 0-127) read accumulator i mod 2 and write the plane
 // while the MMAs of tile i + 1 run.  Per tile the MMAs run in the same order
 // as one CTA per tile would, so the planes are bitwise the same.
 constexpr int TC_THREADS = 192;
-constexpr int ACC_COLS = 2 * TBN;
 
 struct TileOf {
     int s;       // signal
@@ -147,23 +160,27 @@ struct TileOf {
     bool skip;   // reset pass: signal not flagged
 };
 
+template <int BN>
 __device__ __forceinline__ TileOf tile_of(long long t, int nrow, const long long* tprefix, int nsig,
                                           const DevSig* sigs, int flagged) {
     TileOf o;
     const long long ft = t / nrow;
     o.r0 = (int)(t - ft * nrow) * TBM;
     o.s = find_tile_sig(tprefix, nsig, ft);
-    o.n0 = (int)((ft - tprefix[o.s]) * TBN);
+    o.n0 = (int)((ft - tprefix[o.s]) * BN);
     o.skip = flagged && !sigs[o.s].reanalyze;
     return o;
 }
 
+template <int BN>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_analysis_tc(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
                   const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
                   int Kp, int a, int Mrp, int nsig, const long long* __restrict__ tprefix,
                   const int* __restrict__ brow, const DevSig* __restrict__ sigs, int dict,
                   long long ntiles, int nrow, int* __restrict__ err, int flagged) {
+    using Cfg = TcCfg<BN>;
+    constexpr int STAGES = Cfg::STAGES, STAGE_BYTES = Cfg::STAGE_BYTES, ACC_COLS = Cfg::ACC_COLS;
     extern __shared__ unsigned char smem_raw[];
     const unsigned raw = smem_u32(smem_raw);
     const unsigned base = (raw + 1023u) & ~1023u;
@@ -176,7 +193,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         reinterpret_cast<volatile unsigned*>(gbase + STAGES * STAGE_BYTES + 16 * STAGES + 40);
     __shared__ volatile int failed;
     __shared__ volatile int tile_ok;  // epilogue: the accumulator of this tile is ready
-    float* stg = reinterpret_cast<float*>(gbase + STG_OFF);
+    float* stg = reinterpret_cast<float*>(gbase + Cfg::STG_OFF);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = Kp / TBK;
@@ -211,7 +228,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             long long kc = 0;  // K blocks issued by this CTA
             for (long long t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
-                const TileOf T = tile_of(t, nrow, tprefix, nsig, sigs, flagged);
+                const TileOf T = tile_of<BN>(t, nrow, tprefix, nsig, sigs, flagged);
                 if (T.skip) continue;
                 const int row0 = brow[T.s] + T.n0;
                 for (int kb = 0; kb < nk; ++kb, ++kc) {
@@ -231,7 +248,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tma_load_2d(sb, &tAh, k0, T.r0, fb);
                     tma_load_2d(sb + TILE_BYTES, &tAl, k0, T.r0, fb);
                     tma_load_2d(sb + 2 * TILE_BYTES, &tBh, rr, row0 + q, fb);
-                    tma_load_2d(sb + 3 * TILE_BYTES, &tBl, rr, row0 + q, fb);
+                    tma_load_2d(sb + 2 * TILE_BYTES + Cfg::B_BYTES, &tBl, rr, row0 + q, fb);
                 }
             }
             if (failed) {
@@ -244,10 +261,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else if (warp == 5) {
         // ---- MMA issuer ----------------------------------------------------
         if (lane == 0) {
-            const unsigned idesc = idesc_bf16(TBM, TBN);
+            const unsigned idesc = idesc_bf16(TBM, BN);
             long long kc = 0, tc = 0;
             for (long long t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
-                const TileOf T = tile_of(t, nrow, tprefix, nsig, sigs, flagged);
+                const TileOf T = tile_of<BN>(t, nrow, tprefix, nsig, sigs, flagged);
                 if (T.skip) continue;
                 const int b = (int)(tc & 1);
                 const unsigned use = (unsigned)(tc >> 1);
@@ -256,7 +273,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const unsigned acc = tmem + (unsigned)(b * TBN);
+                const unsigned acc = tmem + (unsigned)(b * BN);
                 for (int kb = 0; kb < nk; ++kb, ++kc) {
                     const int st = (int)(kc % STAGES);
                     const unsigned rnd = (unsigned)(kc / STAGES);
@@ -272,7 +289,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         const unsigned long long ah = sw128_desc(sb + off);
                         const unsigned long long al = sw128_desc(sb + TILE_BYTES + off);
                         const unsigned long long bh = sw128_desc(sb + 2 * TILE_BYTES + off);
-                        const unsigned long long bl = sw128_desc(sb + 3 * TILE_BYTES + off);
+                        const unsigned long long bl =
+                            sw128_desc(sb + 2 * TILE_BYTES + Cfg::B_BYTES + off);
                         umma_bf16(acc, ah, bh, idesc, (kb | kk) != 0);
                         umma_bf16(acc, ah, bl, idesc, 1);
                         umma_bf16(acc, al, bh, idesc, 1);
@@ -296,7 +314,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int rl = warp * 32 + lane;
         long long tc = 0;
         for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-            const TileOf T = tile_of(t, nrow, tprefix, nsig, sigs, flagged);
+            const TileOf T = tile_of<BN>(t, nrow, tprefix, nsig, sigs, flagged);
             if (T.skip) continue;
             const int b = (int)(tc & 1);
             const unsigned use = (unsigned)(tc >> 1);
@@ -313,10 +331,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             float2* plane = S.plane[dict];
             const int mb = T.r0 >> 1;  // first bin of the tile
 #pragma unroll 1
-            for (int c0 = 0; c0 < TBN; c0 += 32) {
+            for (int c0 = 0; c0 < BN; c0 += 32) {
                 unsigned v[32];
                 const unsigned taddr =
-                    tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(b * TBN + c0);
+                    tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(b * BN + c0);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, "
                     "%9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, "
@@ -395,8 +413,6 @@ __global__ void k_split_segment(const DevSig* __restrict__ sigs, const long long
 
 }  // namespace
 
-int analysis_tc_smem() { return TC_SMEM; }
-
 cudaError_t launch_split_rows(const float* src, int rows, int cols, int src_ld, int cols_p,
                               void* hi, void* lo, cudaStream_t st) {
     const long long n = (long long)rows * cols_p;
@@ -414,17 +430,29 @@ cudaError_t launch_split_segments(const DevSig* d_sigs, int nsig, const long lon
     return cudaGetLastError();
 }
 
-cudaError_t launch_analysis_tc(const void* tmaps /* 4 CUtensorMap */, int Arows, int Kp, int a,
-                               int Mrp, int nsig, const long long* d_tile_prefix, const int* d_brow,
-                               const DevSig* d_sigs, int dict, long long total_tiles, int* d_err,
-                               cudaStream_t st, int flagged) {
+int analysis_tc_frames(long long nrow, long long tiles256, long long frames128,
+                       long long frames256, int num_sms) {
+    // 256-frame tiles when every SM gets at least four of them and the wider
+    // tiles pad the frames by at most a quarter more than 128-frame tiles do
+    // (on GB300 the 256-frame form was faster on a batch of 256 signals even
+    // at 14 % more padded frames: the operand loads, not the MMAs, set the
+    // pace there)
+    return nrow * tiles256 >= 4ll * num_sms && 4 * frames256 <= 5 * frames128 ? 256 : 128;
+}
+
+cudaError_t launch_analysis_tc(const void* tmaps /* 4 CUtensorMap */, int bn, int Arows, int Kp,
+                               int a, int Mrp, int nsig, const long long* d_tile_prefix,
+                               const int* d_brow, const DevSig* d_sigs, int dict,
+                               long long total_tiles, int* d_err, cudaStream_t st, int flagged) {
     if (total_tiles <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_analysis_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         TC_SMEM);
+    if (bn != 128 && bn != 256) return cudaErrorInvalidValue;
+    auto kf = bn == 256 ? k_analysis_tc<256> : k_analysis_tc<128>;
+    const int smem = bn == 256 ? TcCfg<256>::SMEM : TcCfg<128>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const CUtensorMap* m = static_cast<const CUtensorMap*>(tmaps);
-    // one CTA per SM (the shared memory allows no second one), each looping
-    // over the tiles
+    // one CTA per SM (the shared memory allows no second one, so the CTA
+    // holds the SM's tensor memory alone), each looping over the tiles
     int dev = 0, sms = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -432,9 +460,8 @@ cudaError_t launch_analysis_tc(const void* tmaps /* 4 CUtensorMap */, int Arows,
     const int nrow = Arows / TBM;
     const long long ntiles = total_tiles * nrow;
     const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
-    k_analysis_tc<<<grid, TC_THREADS, TC_SMEM, st>>>(m[0], m[1], m[2], m[3], Kp, a, Mrp, nsig,
-                                                     d_tile_prefix, d_brow, d_sigs, dict, ntiles,
-                                                     nrow, d_err, flagged);
+    kf<<<grid, TC_THREADS, smem, st>>>(m[0], m[1], m[2], m[3], Kp, a, Mrp, nsig, d_tile_prefix,
+                                       d_brow, d_sigs, dict, ntiles, nrow, d_err, flagged);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,7 @@ struct mp_state {
     mp_atom* d_atoms;
     double* d_errs;
     double* d_scalar;
+    double* d_epart;         // [B][ENERGY_PARTS]: partial sums of the FP64 signal energies
     double time_limit_s;
     long long reset_it;      // resets (Alg. 2): selections per reset, 0 = off
     double reset_db;         // resets once 10 log10(E/E_out) < reset_db (< 0), 0 = off
@@ -57,6 +58,7 @@ struct mp_state {
     int* d_brow;             // [W][B]: first view row of each signal's frame 0
     long long* d_tc_prefix[MAXW];
     long long total_tc_tiles[MAXW];
+    int tc_frames[MAXW];     // frames per tensor-core analysis tile (128 or 256)
     int* d_err;
     alignas(64) unsigned char tmB[MAXW][2][128];
 };
@@ -86,6 +88,7 @@ void state_free(mp_state* s) {
     if (s->d_atoms) cudaFree(s->d_atoms);
     if (s->d_errs) cudaFree(s->d_errs);
     if (s->d_scalar) cudaFree(s->d_scalar);
+    if (s->d_epart) cudaFree(s->d_epart);
     if (s->d_xhi) cudaFree(s->d_xhi);
     if (s->d_xlo) cudaFree(s->d_xlo);
     if (s->d_seg) cudaFree(s->d_seg);
@@ -140,6 +143,7 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
     s->d_brow = nullptr;
     s->d_err = nullptr;
     memset(s->d_tc_prefix, 0, sizeof(s->d_tc_prefix));
+    memset(s->tc_frames, 0, sizeof(s->tc_frames));
     memset(s->d_tile_prefix, 0, sizeof(s->d_tile_prefix));
     memset(s->d_frame_prefix, 0, sizeof(s->d_frame_prefix));
     s->plan = p;
@@ -152,6 +156,7 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
     s->d_atoms = nullptr;
     s->d_errs = nullptr;
     s->d_scalar = nullptr;
+    s->d_epart = nullptr;
     s->cap = 0;
     s->time_limit_s = 0.0;
     s->reset_it = 0;
@@ -240,6 +245,7 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
     if (e == cudaSuccess) e = cudaMalloc(&s->d_scalar, sizeof(double) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_epart, sizeof(double) * ENERGY_PARTS * B);
     if (e == cudaSuccess && (p->flags & MP_ANALYSIS_BF16X3)) {
         // padded BF16 segments: seg[j] = x(j - pad), offsets multiples of a_max
         int amax = 0, wmax = 0, kmax64 = 0;
@@ -275,8 +281,15 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
             e = cudaMemcpyAsync(s->d_brow, brow.data(), sizeof(int) * W * B, cudaMemcpyHostToDevice,
                                 st);
         for (int w = 0; w < W && e == cudaSuccess; ++w) {
+            long long t256 = 0, f128 = 0;
+            for (int b = 0; b < B; ++b) {
+                t256 += (s->hs[b].N[w] + 255) / 256;
+                f128 += (s->hs[b].N[w] + 127) / 128 * 128;
+            }
+            const int bn = analysis_tc_frames(p->Arows[w] / 128, t256, f128, t256 * 256, p->num_sms);
+            s->tc_frames[w] = bn;
             std::vector<long long> tp(B + 1, 0);
-            for (int b = 0; b < B; ++b) tp[b + 1] = tp[b] + (s->hs[b].N[w] + 127) / 128;
+            for (int b = 0; b < B; ++b) tp[b + 1] = tp[b] + (s->hs[b].N[w] + bn - 1) / bn;
             s->total_tc_tiles[w] = tp[B];
             e = cudaMalloc(&s->d_tc_prefix[w], sizeof(long long) * (B + 1));
             if (e == cudaSuccess)
@@ -285,8 +298,8 @@ int state_create(const mp_plan* p, int B, const int64_t* L, mp_state** out) {
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             const unsigned long long aw = (unsigned long long)p->a[w];
             if (e == cudaSuccess &&
-                (!encode_bf16_map(s->tmB[w][0], s->d_xhi, aw, tot / aw, aw * 2) ||
-                 !encode_bf16_map(s->tmB[w][1], s->d_xlo, aw, tot / aw, aw * 2))) {
+                (!encode_bf16_map(s->tmB[w][0], s->d_xhi, aw, tot / aw, aw * 2, (unsigned)bn) ||
+                 !encode_bf16_map(s->tmB[w][1], s->d_xlo, aw, tot / aw, aw * 2, (unsigned)bn))) {
                 state_free(s);
                 return MP_ECUDA;
             }
@@ -338,7 +351,7 @@ int analyze_impl(const mp_plan* p, mp_state** state, int B, const float* const* 
     cudaStream_t st = p->stream;
     for (int b = 0; b < B; ++b)
         CKR(cudaMemcpyAsync((void*)s->hs[b].x, x[b], sizeof(float) * L[b], kind, st));
-    CKR(launch_energy(s->d_sigs, B, nullptr, 0, st));
+    CKR(launch_energy(s->d_sigs, B, s->d_epart, st));
     rc = analysis_pass(s, 0);
     if (rc) return rc;
     if (kind == cudaMemcpyHostToDevice) CKR(cudaStreamSynchronize(st));
@@ -364,9 +377,9 @@ int analysis_pass(mp_state* s, int flagged) {
             memcpy(maps[1], p->tmA[w][1], 128);
             memcpy(maps[2], s->tmB[w][0], 128);
             memcpy(maps[3], s->tmB[w][1], 128);
-            CKR(launch_analysis_tc(maps, p->Arows[w], p->Kp64[w], D.a, D.Mrp, B, s->d_tc_prefix[w],
-                                   s->d_brow + (size_t)w * B, s->d_sigs, w, s->total_tc_tiles[w],
-                                   s->d_err, st, flagged));
+            CKR(launch_analysis_tc(maps, s->tc_frames[w], p->Arows[w], p->Kp64[w], D.a, D.Mrp, B,
+                                   s->d_tc_prefix[w], s->d_brow + (size_t)w * B, s->d_sigs, w,
+                                   s->total_tc_tiles[w], s->d_err, st, flagged));
         } else if (p->flags & MP_COEF_FP64) {
             CKR(launch_analysis_dgemm(p->d_A64[w], p->Arows[w], p->Akp[w], D.wlen, D.a, D.Mrp, B,
                                       s->d_tile_prefix[w], s->d_sigs, w, s->total_tiles[w], st,
@@ -539,7 +552,7 @@ static int reset_pass(mp_state* s, const std::vector<int>& sigs) {
         CKR(cudaMemcpyAsync((char*)(s->d_sigs + b) + offsetof(DevSig, reanalyze), &one, sizeof(int),
                             cudaMemcpyHostToDevice, st));
     }
-    CKR(launch_reset_residual(s->d_sigs, s->B, st));
+    CKR(launch_reset_residual(s->d_sigs, s->B, s->d_epart, st));
     int rc = analysis_pass(s, 1);
     if (rc) return rc;
     const int zero = 0;

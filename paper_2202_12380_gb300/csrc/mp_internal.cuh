@@ -130,10 +130,13 @@ cudaError_t launch_analysis_dgemm(const double* A, int Arows, int Kp, int w_len,
                                   int nsig, const long long* d_tile_prefix, const DevSig* d_sigs,
                                   int dict, long long total_frame_tiles, cudaStream_t st,
                                   int flagged = 0);
-cudaError_t launch_energy(const DevSig* d_sigs, int nsig, double* d_partials, int nparts,
-                          cudaStream_t st);
+// E_0 = E = ||x||^2 (FP64) of every signal and a fresh pursuit state.
+// d_part: scratch of nsig * ENERGY_PARTS doubles (partial sums).
+constexpr int ENERGY_PARTS = 64;
+cudaError_t launch_energy(DevSig* d_sigs, int nsig, double* d_part, cudaStream_t st);
 // reset pass: r = x - y for flagged signals, then E = E_out = ||r||^2
-cudaError_t launch_reset_residual(DevSig* d_sigs, int nsig, cudaStream_t st);
+// (d_part as for launch_energy)
+cudaError_t launch_reset_residual(DevSig* d_sigs, int nsig, double* d_part, cudaStream_t st);
 cudaError_t launch_tree_build(const DevPlan& P, const DevSig* d_sigs, int nsig,
                               const long long* d_frame_prefix, long long total_frames, int dict,
                               cudaStream_t st, int flagged = 0);
@@ -160,21 +163,25 @@ cudaError_t launch_synth(const DevPlan& P, const DevSig* d_sig, long long natoms
 cudaError_t launch_resid_energy(const DevSig* d_sig, const float* y, long long L,
                                 double* d_partials, int nparts, cudaStream_t st);
 
-// tensor-core (split-BF16) analysis, mp_analysis_tc.cu
-int analysis_tc_smem();
+// tensor-core (split-BF16) analysis, mp_analysis_tc.cu.  Tiles are 128 rows
+// of A by bn = 128 or 256 frames; analysis_tc_frames picks bn from the row
+// tiles, the tile count with 256 frames and the frames both widths cover.
+int analysis_tc_frames(long long nrow, long long tiles256, long long frames128,
+                       long long frames256, int num_sms);
 cudaError_t launch_split_rows(const float* src, int rows, int cols, int src_ld, int cols_p,
                               void* hi, void* lo, cudaStream_t st);
 cudaError_t launch_split_segments(const DevSig* d_sigs, int nsig, const long long* seg_off,
                                   const long long* seg_len, int pad, void* hi, void* lo,
                                   cudaStream_t st, int flagged = 0);
-cudaError_t launch_analysis_tc(const void* tmaps, int Arows, int Kp, int a, int Mrp, int nsig,
-                               const long long* d_tile_prefix, const int* d_brow,
+cudaError_t launch_analysis_tc(const void* tmaps, int bn, int Arows, int Kp, int a, int Mrp,
+                               int nsig, const long long* d_tile_prefix, const int* d_brow,
                                const DevSig* d_sigs, int dict, long long total_tiles, int* d_err,
                                cudaStream_t st, int flagged = 0);
-// encodes a 2-D BF16 tensor map with a 64 x 128 box and 128-byte swizzle
-// (mp_plan.cu); returns false on failure
+// encodes a 2-D BF16 tensor map with a 64 x box_rows box and 128-byte
+// swizzle (mp_plan.cu); returns false on failure
 bool encode_bf16_map(void* map, const void* base, unsigned long long inner,
-                     unsigned long long outer, unsigned long long row_bytes);
+                     unsigned long long outer, unsigned long long row_bytes,
+                     unsigned box_rows = 128);
 
 size_t mp_loop_smem_bytes(const DevPlan& P, int T, int threads, int cs);
 int mp_loop_threads(int nsig, int num_sms);

@@ -224,7 +224,8 @@ void plan_free(mp_plan* p) {
 }  // namespace
 
 bool mpg::encode_bf16_map(void* map, const void* base, unsigned long long inner,
-                          unsigned long long outer, unsigned long long row_bytes) {
+                          unsigned long long outer, unsigned long long row_bytes,
+                          unsigned box_rows) {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
         cudaDriverEntryPointQueryResult q;
@@ -239,7 +240,7 @@ bool mpg::encode_bf16_map(void* map, const void* base, unsigned long long inner,
     }
     cuuint64_t dims[2] = {inner, outer};
     cuuint64_t strides[1] = {row_bytes};
-    cuuint32_t box[2] = {64, 128};
+    cuuint32_t box[2] = {64, box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                     const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,

@@ -17,8 +17,9 @@
 // address is obtained once per device with cudaGetSymbolAddress (with that
 // device current) and passed to the kernels.  Every call on a device shares
 // the array and finds the previous call's contents there; all regions are
-// rewritten from scratch by each call (descriptor, signal copy, planes
-// including padding bins, all tree levels), so nothing is carried over.
+// rewritten from scratch by each call (descriptor, signal copy, energy
+// partial sums, planes including padding bins, all tree levels), so nothing
+// is carried over.
 // Calls that overlap on the GPU (other streams, other host threads) race on
 // the array and must be serialised by the caller.
 #include <cuda_runtime.h>
@@ -50,7 +51,7 @@ struct StaticTables {
 };
 
 struct StaticLayout {
-    size_t o_sig, o_order, o_tp, o_fp, o_errs, total;
+    size_t o_sig, o_order, o_tp, o_fp, o_epart, o_errs, total;
     size_t o_plane[MAXW], o_l0[MAXW], o_l1[MAXW], o_x;
 };
 
@@ -162,6 +163,8 @@ extern "C" int mp_decompose_static(const mp_plan* p, const float* x_dev, int64_t
     off = al(off + sizeof(long long) * 2 * MAXW);
     lay.o_fp = off;
     off = al(off + sizeof(long long) * 2 * MAXW);
+    lay.o_epart = off;
+    off = al(off + sizeof(double) * ENERGY_PARTS);
     unsigned long long P = 0;
     for (int w = 0; w < W; ++w) {
         const DevDict& D = p->dp.d[w];
@@ -224,7 +227,7 @@ extern "C" int mp_decompose_static(const mp_plan* p, const float* x_dev, int64_t
     k_static_init<<<1, 32, 0, st>>>(t, base, lay, W);
     CKS(cudaGetLastError());
     CKS(cudaMemcpyAsync(base + lay.o_x, x_dev, sizeof(float) * L, cudaMemcpyDeviceToDevice, st));
-    CKS(launch_energy(d_sig, 1, nullptr, 0, st));
+    CKS(launch_energy(d_sig, 1, reinterpret_cast<double*>(base + lay.o_epart), st));
     for (int w = 0; w < W; ++w) {
         const DevDict& D = p->dp.d[w];
         CKS(launch_analysis_sgemm(p->d_A[w], p->Arows[w], p->Akp[w], D.wlen, D.a, D.Mrp, 1,

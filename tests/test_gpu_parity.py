@@ -192,6 +192,24 @@ def test_batched_uneven_lengths():
             assert atoms.size == ref.n_atoms and stop == ref.stop
 
 
+def test_signal_energy_batch():
+    """E_0 = ||x||^2 (FP64, summed over the GPU in 64 segments per signal):
+    a signal with fewer samples per segment (16) than threads per block, one
+    whose segments (3078 samples) are not a multiple of the block, and a
+    long one, against numpy's FP64 sum."""
+    dicts = [(inputs.blackman(128), 32, 128)]
+    lens = [1024, 3 * (1 << 16) + 384, 1 << 20]
+    xs = [inputs.as_f32(inputs.mixture(L, 70 + i, fs=16000.0)) for i, L in enumerate(lens)]
+    plan = _plan(dicts, 1e-4)
+    st = mg.mp_analyze(plan, [torch.from_numpy(x).cuda() for x in xs])
+    n, stop, q = mg.mp_run(st, 1, 400.0)
+    for b, x in enumerate(xs):
+        errs = mg.mp_get_errors(st, b)
+        E0 = errs[-1] * 10 ** (q[b] / 10)
+        ref = float(np.sum(x.astype(np.float64) ** 2))
+        assert E0 == pytest.approx(ref, rel=1e-11), (b, E0, ref)
+
+
 def test_stop_rules_gpu():
     dicts = [(inputs.blackman(128), 32, 128)]
     L = 4096
@@ -349,6 +367,44 @@ def test_analysis_bf16x3_batched_uneven():
             ref = cmp.dgt(x.astype(np.float64), g, a, M)
             got = mg.mp_state_coefficients(st, b, w)
             assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 2e-5
+
+
+def _kernel_names(fn):
+    """Names of the CUDA kernels fn() launches (torch profiler); empty when
+    the profiler records no device activity."""
+    from torch.profiler import ProfilerActivity, profile
+
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        fn()
+        torch.cuda.synchronize()
+    return {e.name for e in prof.events() if e.device_type == torch.autograd.DeviceType.CUDA}
+
+
+def test_analysis_bf16x3_wide_tiles_batch():
+    """A batch with many tiles: the two smaller dictionaries take 256-frame
+    tensor-core tiles (64 signals of 2^16 samples: 768 and 640 tiles, no
+    padding), the largest keeps 128-frame tiles (576 tiles of 256 frames
+    would leave SMs with fewer than four).  Sampled signals, including the
+    first and the last, against the FP64 analysis."""
+    _, dicts = _bf16_dicts()
+    B, L = 64, 1 << 16
+    xs = [inputs.as_f32(inputs.mixture(L, 400 + i, fs=16000.0)) for i in range(B)]
+    plan = _plan(dicts, 1e-4, mg.MP_ANALYSIS_BF16X3)
+    dev = [torch.from_numpy(x).cuda() for x in xs]
+    box = {}
+    names = _kernel_names(lambda: box.setdefault("st", mg.mp_analyze(plan, dev)))
+    st = box["st"]
+    tc = {n for n in names if "k_analysis_tc" in n}
+    if names:
+        assert any("k_analysis_tc<256>" in n for n in tc), tc
+        assert any("k_analysis_tc<128>" in n for n in tc), tc
+    for b in sorted({0, 1, 17, 38, B - 2, B - 1}):
+        for w, (g, a, M) in enumerate(dicts):
+            ref = cmp.dgt(xs[b].astype(np.float64), g, a, M)
+            got = mg.mp_state_coefficients(st, b, w)
+            rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+            worst = np.max(np.abs(got - ref)) / np.sqrt(np.mean(np.abs(ref) ** 2))
+            assert rel < 2e-5 and worst < 2e-4, (b, w, rel, worst)
 
 
 def test_mp_bf16x3_decomposition_vs_oracle():
