@@ -129,7 +129,12 @@ int mp_plan_gamma(const mp_plan* plan, int u, float* gamma_host, int64_t cap_flo
  * (reduced rows m = 0 .. M_w/2), E_0 = ||x||^2 in FP64, and the max trees.
  *   B        number of signals (>= 1); each is decomposed independently
  *   x_dev[b] device pointer to L[b] floats (read only during the call's
- *            stream work)
+ *            stream work): device memory of the plan's device, managed or
+ *            page-locked host memory; a pageable host address or memory of
+ *            another device is MP_EINVAL (checked with
+ *            cudaPointerGetAttributes when the plan's stream is not being
+ *            captured; the signals are copied into the state by one kernel
+ *            per 256 signals)
  * If *state is NULL a new state is allocated; if it is non-NULL it must come
  * from the same plan with the same B and lengths and is reused (all previous
  * atoms are discarded).  Asynchronous on the plan's stream; reusing a state,

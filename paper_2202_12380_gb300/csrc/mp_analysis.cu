@@ -238,6 +238,25 @@ __global__ void k_sqnorm_final(DevSig* sigs, int nsig, const double* __restrict_
     }
 }
 
+// copy of up to GATHER_MAX signals (device to device) in one launch: block
+// row y copies signal y, 16-byte accesses when both ends are 16-byte aligned
+__global__ void __launch_bounds__(256) k_gather_signals(GatherArgs g) {
+    const int b = blockIdx.y;
+    const float* __restrict__ src = g.src[b];
+    float* __restrict__ dst = g.dst[b];
+    const long long n = g.len[b];
+    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long step = (long long)gridDim.x * blockDim.x;
+    long long done = 0;
+    if (((reinterpret_cast<size_t>(src) | reinterpret_cast<size_t>(dst)) & 15) == 0) {
+        const long long n4 = n >> 2;
+        for (long long i = i0; i < n4; i += step)
+            reinterpret_cast<float4*>(dst)[i] = __ldg(reinterpret_cast<const float4*>(src) + i);
+        done = n4 << 2;
+    }
+    for (long long i = done + i0; i < n; i += step) dst[i] = src[i];
+}
+
 // level 0 (per 32-bin chunk) and level 1 (per frame) of dictionary `dict`,
 // one warp per frame (C2: float2 or double2 planes)
 template <typename C2>
@@ -257,19 +276,27 @@ __global__ void k_tree_build(DevPlan P, const DevSig* __restrict__ sigs, int nsi
     Key* l0 = S.l0[dict] + n * D.nch;
     const unsigned fb = S.fbase[dict] + ((unsigned)n << D.msh);
     Key best = 0ull;
-    for (int ch = 0; ch < D.nch; ++ch) {
-        const int m = ch * CHUNK + lane;
-        const C2 v = row[m];
-        const Key k = (m < D.Mr) ? make_key_sel(v, fb + m, m, D, gam, P.pedantic) : 0ull;
-        const Key r = warp_max_key(k);
-        if (lane == 0) l0[ch] = r;
-        best = r > best ? r : best;
+    // four chunks' loads in flight per warp (one at a time left the planes'
+    // read at about a third of the HBM bandwidth)
+    constexpr int U = 4;
+    for (int ch0 = 0; ch0 < D.nch; ch0 += U) {
+        C2 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (ch0 + u < D.nch) v[u] = row[(ch0 + u) * CHUNK + lane];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (ch0 + u >= D.nch) break;
+            const int m = (ch0 + u) * CHUNK + lane;
+            const Key k = (m < D.Mr) ? make_key_sel(v[u], fb + m, m, D, gam, P.pedantic) : 0ull;
+            const Key r = warp_max_key(k);
+            if (lane == 0) l0[ch0 + u] = r;
+            best = r > best ? r : best;
+        }
     }
     if (lane == 0) S.l1[dict][n] = best;
 }
 
-// reset pass, one block per signal: r = x - y and E = E_out = ||r||^2
-// (FP64, fixed order) for the flagged signals
 }  // namespace
 
 cudaError_t launch_analysis_sgemm(const float* A, int Arows, int Kp, int w_len, int a, int Mrp,
@@ -291,6 +318,13 @@ cudaError_t launch_analysis_dgemm(const double* A, int Arows, int Kp, int w_len,
     dim3 grid((unsigned)total_frame_tiles, (unsigned)(Arows / BM));
     k_analysis_gemm<double, double2><<<grid, 256, 0, st>>>(A, Kp, w_len, a, Mrp, nsig,
                                                            d_tile_prefix, d_sigs, dict, flagged);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_signals(const GatherArgs& g, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (n > GATHER_MAX) return cudaErrorInvalidValue;
+    k_gather_signals<<<dim3(64, (unsigned)n), 256, 0, st>>>(g);
     return cudaGetLastError();
 }
 

@@ -336,6 +336,33 @@ int analyze_impl(const mp_plan* p, mp_state** state, int B, const float* const* 
             mpg_set_error("mp_analyze: signal pointer %d is null", b);
             return MP_EINVAL;
         }
+    cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
+    if (kind == cudaMemcpyDeviceToDevice &&
+        cudaStreamIsCapturing(p->stream, &capst) == cudaSuccess &&
+        capst == cudaStreamCaptureStatusNone) {
+        // the signals are read by a kernel: each must be memory this device
+        // can address (its own device memory, managed or page-locked host
+        // memory).  Checked outside stream capture only, where no query
+        // can disturb a capture.
+        for (int b = 0; b < B; ++b) {
+            cudaPointerAttributes pa;
+            if (cudaPointerGetAttributes(&pa, x[b]) != cudaSuccess) {
+                cudaGetLastError();
+                mpg_set_error("mp_analyze: signal pointer %d is not a CUDA address", b);
+                return MP_EINVAL;
+            }
+            if (pa.type == cudaMemoryTypeUnregistered) {
+                mpg_set_error("mp_analyze: signal %d is in pageable host memory (use "
+                              "mp_analyze_host)", b);
+                return MP_EINVAL;
+            }
+            if (pa.type == cudaMemoryTypeDevice && pa.device != p->device) {
+                mpg_set_error("mp_analyze: signal %d is on device %d, the plan's is %d", b,
+                              pa.device, p->device);
+                return MP_EINVAL;
+            }
+        }
+    }
     mp_state* s = *state;
     if (s) {
         bool same = s->plan == p && s->B == B;
@@ -349,8 +376,22 @@ int analyze_impl(const mp_plan* p, mp_state** state, int B, const float* const* 
         if (rc) return rc;
     }
     cudaStream_t st = p->stream;
-    for (int b = 0; b < B; ++b)
-        CKR(cudaMemcpyAsync((void*)s->hs[b].x, x[b], sizeof(float) * L[b], kind, st));
+    if (kind == cudaMemcpyDeviceToDevice) {
+        // one launch per GATHER_MAX signals instead of one copy per signal
+        GatherArgs g;
+        for (int b0 = 0; b0 < B; b0 += GATHER_MAX) {
+            const int n = std::min(GATHER_MAX, B - b0);
+            for (int i = 0; i < n; ++i) {
+                g.src[i] = x[b0 + i];
+                g.dst[i] = const_cast<float*>(s->hs[b0 + i].x);
+                g.len[i] = L[b0 + i];
+            }
+            CKR(launch_gather_signals(g, n, st));
+        }
+    } else {
+        for (int b = 0; b < B; ++b)
+            CKR(cudaMemcpyAsync((void*)s->hs[b].x, x[b], sizeof(float) * L[b], kind, st));
+    }
     CKR(launch_energy(s->d_sigs, B, s->d_epart, st));
     rc = analysis_pass(s, 0);
     if (rc) return rc;

@@ -130,6 +130,16 @@ cudaError_t launch_analysis_dgemm(const double* A, int Arows, int Kp, int w_len,
                                   int nsig, const long long* d_tile_prefix, const DevSig* d_sigs,
                                   int dict, long long total_frame_tiles, cudaStream_t st,
                                   int flagged = 0);
+// device-to-device copy of up to GATHER_MAX signals in one launch (the
+// pointers and lengths travel as kernel parameters, so the launch can be
+// captured in a CUDA graph)
+constexpr int GATHER_MAX = 256;
+struct GatherArgs {
+    const float* src[GATHER_MAX];
+    float* dst[GATHER_MAX];
+    long long len[GATHER_MAX];
+};
+cudaError_t launch_gather_signals(const GatherArgs& g, int n, cudaStream_t st);
 // E_0 = E = ||x||^2 (FP64) of every signal and a fresh pursuit state.
 // d_part: scratch of nsig * ENERGY_PARTS doubles (partial sums).
 constexpr int ENERGY_PARTS = 64;

@@ -301,6 +301,30 @@ def test_analyze_host_matches_device():
     assert np.array_equal(mg.mp_get_atoms(st, 0), mg.mp_get_atoms(st_h, 0))
 
 
+def test_analyze_device_entry_checks_signal_memory():
+    """mp_analyze reads the signals with a kernel: a pageable host address is
+    refused with MP_EINVAL (nothing launched, no state made); page-locked
+    host memory is readable by the device and gives the device result."""
+    import ctypes as C
+
+    L, dicts = _workload_small("multi3")
+    x = inputs.as_f32(inputs.mixture(L, 92, fs=16000.0))
+    plan = _plan(dicts, 1e-4)
+    lens = (C.c_int64 * 1)(L)
+    st = mg.State(plan, [L])
+    rc = mg.lib().mp_analyze(plan.handle, C.byref(st.handle), 1, (C.c_void_p * 1)(x.ctypes.data),
+                             lens)
+    assert rc == mg.MP_EINVAL and not st.handle
+    assert "pageable" in mg.lib().mp_last_error().decode()
+    pinned = torch.from_numpy(x).pin_memory()
+    rc = mg.lib().mp_analyze(plan.handle, C.byref(st.handle), 1,
+                             (C.c_void_p * 1)(pinned.data_ptr()), lens)
+    assert rc == 0 and st.handle
+    ref = mg.mp_analyze(plan, [torch.from_numpy(x).cuda()])
+    for w in range(len(dicts)):
+        assert np.array_equal(mg.mp_state_coefficients(st, 0, w), mg.mp_state_coefficients(ref, 0, w))
+
+
 @pytest.mark.parametrize("cluster", [1, 4, 16])
 @pytest.mark.parametrize("kind", ["multi3", "mixed"])
 def test_mp_parity_launch_shapes(kind, cluster):
