@@ -350,7 +350,9 @@ def run_gpu(args):
     stream.synchronize()
     n0, _, _ = mg.mp_get_status(state)
 
-    launches_per_step = 1 + 2 * W + 1
+    # signal gather, energy partials + sum, (BF16 split), one GEMM and one
+    # tree build per dictionary, the MP loop
+    launches_per_step = 3 + (1 if args.analysis == "bf16x3" else 0) + 2 * W + 1
     clocks = ClockSampler(dev)
     clocks.start()
     if ws > 1:
