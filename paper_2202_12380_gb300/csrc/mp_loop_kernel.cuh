@@ -12,8 +12,11 @@
 // Level 0 (per frame and 32-bin chunk) and level 1 (per frame) live in
 // global memory next to the coefficient planes; the top level (one key per
 // frame, or per group of 2^gshift frames of a single CTA whose frames do not
-// fit) lives in shared memory and is scanned every iteration.  The selected
-// coefficient itself is read from its plane.
+// fit) lives in shared memory and is scanned every iteration.  It is held as
+// two word arrays, scores and inverted flat indices: the scan reads only the
+// scores, since top-level positions are ordered like flat indices (by
+// dictionary, then frame), so among equal scores the first position holds
+// the largest key.  The selected coefficient itself is read from its plane.
 //
 // One iteration:
 //   1. the CTA's best key: warp 0 alone scans a cluster CTA's top level,
@@ -62,6 +65,7 @@ namespace mpg {
 namespace {
 
 constexpr int MAXL0 = 4;   // level-0 entries held per lane (larger frames reload)
+constexpr unsigned NOPOS = 0xffffffffu;  // no top-level position
 constexpr int CB = 4;      // touched chunks per batch of loads
 
 // One dictionary's part of an iteration's update.  Term 0 is the selected
@@ -438,8 +442,21 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
     __syncthreads();
     const int T = ltb[W];
     const int gsh = sgs;
-    Key* top = reinterpret_cast<Key*>(smem_raw);
-    DevClass* scls = reinterpret_cast<DevClass*>(top + ((T + 1) & ~1));
+    // top level: score words tops[0 .. T), inverted flat indices topl[0 .. T)
+    unsigned* tops = reinterpret_cast<unsigned*>(smem_raw);
+    unsigned* topl = tops + ((T + 1) & ~1);
+    auto set_top = [&](int i, Key key) {
+        tops[i] = (unsigned)(key >> 32);
+        topl[i] = (unsigned)key;
+    };
+    // warp-wide best top-level key from each lane's best (score, position);
+    // every lane returns it (0 when no lane holds a position)
+    auto top_best = [&](unsigned sc, unsigned pos) -> Key {
+        const unsigned ms = __reduce_max_sync(FULL, pos == NOPOS ? 0u : sc);
+        const unsigned mp = __reduce_min_sync(FULL, (pos != NOPOS && sc == ms) ? pos : NOPOS);
+        return mp == NOPOS ? 0ull : (((Key)ms << 32) | topl[mp]);
+    };
+    DevClass* scls = reinterpret_cast<DevClass*>(topl + ((T + 1) & ~1));
     // the tables start 16-byte aligned (offset from the shared base, so that
     // every pointer below stays a shared-memory pointer)
     const size_t gam_off =
@@ -462,8 +479,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
         const Key* l1 = S.l1[w];
         if (CS > 1) {
             for (int i = tid; i < te - tb; i += NT)
-                top[tb + i] = inb((long long)i * CS + rank, S.N[w], 2, berr)
-                                  ? l1[(long long)i * CS + rank] : 0ull;
+                set_top(tb + i, inb((long long)i * CS + rank, S.N[w], 2, berr)
+                                    ? l1[(long long)i * CS + rank] : 0ull);
         } else {
             const long long Nw = S.N[w];
             for (int i = tid; i < te - tb; i += NT) {
@@ -472,7 +489,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
                 Key m = 0ull;
                 for (long long f = f0; f < f1; ++f)
                     if (inb(f, Nw, 3, berr)) m = l1[f] > m ? l1[f] : m;
-                top[tb + i] = m;
+                set_top(tb + i, m);
             }
         }
     }
@@ -608,10 +625,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
             if (inb(n, S.N[v], 10, berr)) S.l1[v][n] = fr;
             if (CS > 1) {
                 const int ti = ltb[v] + (n >> cs_sh);
-                if (inb(ti, ltb[v + 1], 11, berr)) top[ti] = fr;
+                if (inb(ti, ltb[v + 1], 11, berr)) set_top(ti, fr);
             } else if (gsh == 0) {
                 const int ti = ltb[v] + n;
-                if (inb(ti, ltb[v + 1], 11, berr)) top[ti] = fr;
+                if (inb(ti, ltb[v + 1], 11, berr)) set_top(ti, fr);
             } else {
                 const int gi = ltb[v] + (n >> gsh);
                 const unsigned bit = 1u << (gi & 31);
@@ -671,32 +688,51 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
             // a cluster CTA with at most 256 top-level keys: warp 0 scans them
             // and sends, the other warps go straight to the wait
             if (warp == 0) {
-                Key b[8];
+                // the lane's scores in position order, the first of equal
+                // scores kept
+                unsigned e[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) b[q] = lane + 32 * q < T ? top[lane + 32 * q] : 0ull;
+                for (int q = 0; q < 8; ++q) e[q] = lane + 32 * q < T ? tops[lane + 32 * q] : 0u;
+                unsigned bs = e[0];
+                int bq = 0;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) b[q] = b[q + 4] > b[q] ? b[q + 4] : b[q];
-                b[0] = b[2] > b[0] ? b[2] : b[0];
-                b[1] = b[3] > b[1] ? b[3] : b[1];
-                best = warp_max_key(b[1] > b[0] ? b[1] : b[0]);
+                for (int q = 1; q < 8; ++q)
+                    if (e[q] > bs) {
+                        bs = e[q];
+                        bq = q;
+                    }
+                best = top_best(bs, lane + 32 * bq < T ? (unsigned)(lane + 32 * bq) : NOPOS);
                 if (lane == 0) arm_exchange(xb, vb, xbytes, (unsigned)sizeof(C2));
             }
         } else {
-            // four independent running maxima, merged at the end
-            Key b0 = 0ull, b1 = 0ull, b2 = 0ull, b3 = 0ull;
+            // four independent running maxima of the scores (each keeps the
+            // first of equal scores), merged at the end
+            unsigned s0 = 0u, s1 = 0u, s2 = 0u, s3 = 0u;
+            unsigned p0 = NOPOS, p1 = NOPOS, p2 = NOPOS, p3 = NOPOS;
             int i = tid;
             for (; i + 3 * NT < T; i += 4 * NT) {
-                const Key e0 = top[i], e1 = top[i + NT], e2 = top[i + 2 * NT], e3 = top[i + 3 * NT];
-                b0 = e0 > b0 ? e0 : b0;
-                b1 = e1 > b1 ? e1 : b1;
-                b2 = e2 > b2 ? e2 : b2;
-                b3 = e3 > b3 ? e3 : b3;
+                const unsigned e0 = tops[i], e1 = tops[i + NT], e2 = tops[i + 2 * NT],
+                               e3 = tops[i + 3 * NT];
+                if (e0 > s0 || p0 == NOPOS) { s0 = e0; p0 = (unsigned)i; }
+                if (e1 > s1 || p1 == NOPOS) { s1 = e1; p1 = (unsigned)(i + NT); }
+                if (e2 > s2 || p2 == NOPOS) { s2 = e2; p2 = (unsigned)(i + 2 * NT); }
+                if (e3 > s3 || p3 == NOPOS) { s3 = e3; p3 = (unsigned)(i + 3 * NT); }
             }
-            for (; i < T; i += NT) b0 = top[i] > b0 ? top[i] : b0;
-            b0 = b1 > b0 ? b1 : b0;
-            b2 = b3 > b2 ? b3 : b2;
-            b0 = b2 > b0 ? b2 : b0;
-            const Key r = warp_max_key(b0);
+            for (; i < T; i += NT) {
+                const unsigned e0 = tops[i];
+                if (e0 > s0 || p0 == NOPOS) { s0 = e0; p0 = (unsigned)i; }
+            }
+            // merge: higher score, else lower position (NOPOS is the highest)
+            auto pick = [](unsigned& sa, unsigned& pa, unsigned sb, unsigned pb) {
+                if (pb != NOPOS && (pa == NOPOS || sb > sa || (sb == sa && pb < pa))) {
+                    sa = sb;
+                    pa = pb;
+                }
+            };
+            pick(s0, p0, s1, p1);
+            pick(s2, p2, s3, p3);
+            pick(s0, p0, s2, p2);
+            const Key r = top_best(s0, p0);
             if (lane == 0) wsel[warp] = r;
             if (CS > 1 && tid == 0) arm_exchange(xb, vb, xbytes, (unsigned)sizeof(C2));
             __syncthreads();
@@ -924,7 +960,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1)
 #pragma unroll
                     for (int q = 0; q < 8; ++q) m2 = e8[q] > m2 ? e8[q] : m2;
                 }
-                if (inb(gi, T, 17, berr)) top[gi] = m2;
+                if (inb(gi, T, 17, berr)) set_top(gi, m2);
                 dbits[gi >> 5] = 0u;
             }
             __syncthreads();
