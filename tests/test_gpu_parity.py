@@ -431,6 +431,39 @@ def test_analysis_bf16x3_wide_tiles_batch():
             assert rel < 2e-5 and worst < 2e-4, (b, w, rel, worst)
 
 
+@pytest.mark.parametrize("pedantic", [False, True])
+def test_bf16x3_batch_tree_keys(pedantic):
+    """Max trees of a tensor-core analysis batch (the 64-signal batch with
+    256- and 128-frame tiles): the first atom of every signal is the maximum
+    of its planes (|rho|^2), and sampled signals follow the FP64 oracle's
+    pursuit (plain or pedantic selection) up to a divergence at a near tie
+    of the BF16 analysis precision (oracle gap below 1e-3)."""
+    _, dicts = _bf16_dicts()
+    B, L, K = 64, 1 << 16, 20
+    xs = [inputs.as_f32(inputs.mixture(L, 500 + i, fs=16000.0)) for i in range(B)]
+    flags = mg.MP_ANALYSIS_BF16X3 | (mg.MP_PEDANTIC if pedantic else 0)
+    plan = _plan(dicts, 1e-4, flags)
+    st = mg.mp_analyze(plan, [torch.from_numpy(x).cuda() for x in xs])
+    planes = [[mg.mp_state_coefficients(st, b, w) for w in range(len(dicts))] for b in range(B)]
+    n, stop, q = mg.mp_run(st, K, 200.0)
+    for b in range(B):
+        atoms = mg.mp_get_atoms(st, b)
+        assert atoms.size == K
+        if not pedantic:
+            top = max(float(np.max(np.abs(p) ** 2)) for p in planes[b])
+            a0 = atoms[0]
+            got = abs(planes[b][a0["dict"]][a0["n"], a0["m"]]) ** 2
+            assert got >= top * (1 - 1e-6), (b, got, top)
+    for b in (0, 9, 31, 63):
+        ref = cmp.mp_coef(dicts, xs[b].astype(np.float64), 1e-4, K, 200.0, pedantic=pedantic)
+        atoms = mg.mp_get_atoms(st, b)
+        same = (atoms["dict"] == ref.dict) & (atoms["m"] == ref.m) & (atoms["n"] == ref.n)
+        d = int(np.argmin(same)) if not same.all() else K
+        if d < K:
+            gap = (ref.s1[d] - ref.s2[d]) / ref.s1[d]
+            assert gap < 1e-3, (b, d, gap)
+
+
 def test_mp_bf16x3_decomposition_vs_oracle():
     """Decomposition with the split-BF16 analysis against the FP64 oracle.
     The analysis error (~1e-5 of the coefficient scale) can flip near ties,
