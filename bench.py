@@ -529,7 +529,7 @@ def run_batched(args, mg, torch, ws=1, rank=0):
     shape, tune_ms, work = autotune.tune(plan, xd, k_probe=args.tune_atoms or cfg["kmax"],
                                          target_snr_db=cfg["snr_db"], stream=stream,
                                          repeats=args.tune_repeats, with_work=True)
-    mg.mp_state_set_launch(state, *shape)
+    autotune.apply(state, shape)
     if work is not None:
         mg.mp_state_set_work_hint(state, work)
     mg.mp_run(state, cfg["kmax"], cfg["snr_db"])
@@ -571,7 +571,8 @@ def run_batched(args, mg, torch, ws=1, rank=0):
            "L_total": L_all, "launch_shape": list(shape),
            "launch_order": "most work first (atoms per signal from the tuner's probe of this "
                            "batch)" if work is not None else "longest signal first",
-           "autotune_ms": {"%dx%d" % k: round(v, 3) for k, v in tune_ms.items()},
+           "autotune_ms": {("%dx%d" % k[:2]) + ("/%d keys" % k[2] if k[2] else ""): round(v, 3)
+                           for k, v in tune_ms.items()},
            "mp_loop_ms_default": loop_default_ms,
            "default_launch": "%dx%d, longest signal first" % tuple(default_shape),
            "cuda_graph": True, "atoms_per_step": int(atoms_all), "ms_per_step": t_max * 1e3,

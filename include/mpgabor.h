@@ -192,6 +192,23 @@ int mp_state_set_launch(mp_state* state, int threads, int cluster);
 int mp_state_get_launch(const mp_state* state, int* threads, int* cluster);
 
 /*
+ * Top level of the max tree in a one-CTA-per-signal launch (tuning; the
+ * tree of Sec. 5.1 with its upper level on chip).  The CTA scans one key per
+ * frame each iteration, or one per group of 2^g frames when the signal has
+ * more frames than max_keys (the smallest g that fits; touched groups are
+ * rebuilt from the per-frame keys after each update).  max_keys: a power of
+ * two from 64 to the CTA size's cap (16384 keys for 512 threads, 8192 for
+ * 256, 4096 for 128), or 0 for that cap (or the largest smaller one whose
+ * top level fits in shared memory).  MP_EINVAL for other values, for a
+ * launch with clusters (a cluster CTA holds its own frames ungrouped), or
+ * when the top level does not fit.  mp_state_set_launch resets it to the
+ * default.  mp_state_get_top_keys reports it (0 for cluster launches).
+ * Results do not depend on it.
+ */
+int mp_state_set_top_keys(mp_state* state, int max_keys);
+int mp_state_get_top_keys(const mp_state* state, int* max_keys);
+
+/*
  * Launch order of the signals (tuning, no counterpart in the paper).  With
  * more signals than the GPU runs at once, the MP launch starts the signals
  * in order and a CTA that finishes takes the next; by default the longer

@@ -668,6 +668,41 @@ extern "C" int mp_state_get_launch(const mp_state* s, int* threads, int* cluster
     return MP_OK;
 }
 
+extern "C" int mp_state_set_top_keys(mp_state* s, int max_keys) {
+    if (!s) {
+        mpg_set_error("mp_state_set_top_keys: null state");
+        return MP_EINVAL;
+    }
+    if (s->shape.cs != 1) {
+        mpg_set_error("mp_state_set_top_keys: the launch runs clusters of %d CTAs; the cap "
+                      "applies to one CTA per signal", s->shape.cs);
+        return MP_EINVAL;
+    }
+    LoopShape sh;
+    const bool ok =
+        max_keys == 0
+            ? mp_loop_shape_ok(s->plan->dp, s->hs.data(), s->B, s->shape.threads, 1, &sh)
+            : mp_loop_shape_single_cap(s->plan->dp, s->hs.data(), s->B, s->shape.threads,
+                                       max_keys, &sh);
+    if (!ok) {
+        mpg_set_error("mp_state_set_top_keys: %d is not a power of two from 64 to the cap of "
+                      "%d-thread CTAs, or the top level does not fit in shared memory",
+                      max_keys, s->shape.threads);
+        return MP_EINVAL;
+    }
+    s->shape = sh;
+    return MP_OK;
+}
+
+extern "C" int mp_state_get_top_keys(const mp_state* s, int* max_keys) {
+    if (!s || !max_keys) {
+        mpg_set_error("mp_state_get_top_keys: null argument");
+        return MP_EINVAL;
+    }
+    *max_keys = s->shape.cs == 1 ? s->shape.topcap : 0;
+    return MP_OK;
+}
+
 extern "C" int mp_state_set_work_hint(mp_state* s, const double* work) {
     if (!s) {
         mpg_set_error("mp_state_set_work_hint: null state");

@@ -168,6 +168,10 @@ cudaError_t launch_mp_loop(const DevPlan& P, DevSig* d_sigs, const int* d_order,
 void mp_loop_shape(const DevPlan& P, const DevSig* hs, int B, int num_sms, LoopShape* out);
 bool mp_loop_shape_ok(const DevPlan& P, const DevSig* hs, int B, int threads, int c,
                       LoopShape* out);
+// one CTA per signal with a top level of at most cap keys (a power of two
+// in 64 .. the CTA size's default cap); false if it does not fit
+bool mp_loop_shape_single_cap(const DevPlan& P, const DevSig* hs, int B, int threads, int cap,
+                              LoopShape* out);
 cudaError_t launch_synth(const DevPlan& P, const DevSig* d_sig, long long natoms, float* y,
                          long long L, cudaStream_t st);
 cudaError_t launch_resid_energy(const DevSig* d_sig, const float* y, long long L,

@@ -105,6 +105,27 @@ int mp_loop_threads(int nsig, int num_sms) {
 // largest dynamic shared memory of one CTA on this part
 constexpr size_t SMEM_MAX = 227 * 1024;
 
+// one CTA per signal whose top level holds at most `cap` keys (frames
+// grouped by the smallest 2^gs that fits); cap a power of two in
+// 64 .. loop_topcap(threads)
+bool mp_loop_shape_single_cap(const DevPlan& P, const DevSig* hs, int B, int threads, int cap,
+                              LoopShape* out) {
+    if (threads != 128 && threads != 256 && threads != 512) return false;
+    if (cap < 64 || (cap & (cap - 1)) || cap > loop_topcap(threads)) return false;
+    int tmax = 1;
+    for (int b = 0; b < B; ++b) {
+        const int t = single_top(hs[b], P.W, cap);
+        tmax = t > tmax ? t : tmax;
+    }
+    const size_t sm = mp_loop_smem_bytes(P, tmax, threads, 1);
+    if (sm > SMEM_MAX || mp_loop_max_clusters(threads, 1, sm, P.fp64 != 0) < 1) return false;
+    out->threads = threads;
+    out->cs = 1;
+    out->topcap = cap;
+    out->smem = sm;
+    return true;
+}
+
 // feasibility of a requested launch shape (threads per CTA, cluster size).
 // A single CTA per signal groups its frames so that the top level fits: the
 // cap starts at loop_topcap(threads) and halves while the shared memory
@@ -114,20 +135,8 @@ bool mp_loop_shape_ok(const DevPlan& P, const DevSig* hs, int B, int threads, in
     if (threads != 128 && threads != 256 && threads != 512) return false;
     if (c != 1 && c != 2 && c != 4 && c != 8 && c != 16) return false;
     if (c == 1) {
-        for (int cap = loop_topcap(threads); cap >= 64; cap >>= 1) {
-            int tmax = 1;
-            for (int b = 0; b < B; ++b) {
-                const int t = single_top(hs[b], P.W, cap);
-                tmax = t > tmax ? t : tmax;
-            }
-            const size_t sm = mp_loop_smem_bytes(P, tmax, threads, 1);
-            if (sm > SMEM_MAX || mp_loop_max_clusters(threads, 1, sm, P.fp64 != 0) < 1) continue;
-            out->threads = threads;
-            out->cs = 1;
-            out->topcap = cap;
-            out->smem = sm;
-            return true;
-        }
+        for (int cap = loop_topcap(threads); cap >= 64; cap >>= 1)
+            if (mp_loop_shape_single_cap(P, hs, B, threads, cap, out)) return true;
         return false;
     }
     int lt = 0;

@@ -30,7 +30,7 @@ EXPORTS = [
     "mp_state_coefficients", "mp_run", "mp_run_async", "mp_get_status", "mp_state_set_time_limit",
     "mp_get_atoms", "mp_get_errors", "mp_synthesize", "mp_state_destroy", "mp_last_error",
     "mp_decompose_static", "mp_state_set_resets", "mp_state_set_launch", "mp_state_get_launch",
-    "mp_state_set_work_hint",
+    "mp_state_set_work_hint", "mp_state_set_top_keys", "mp_state_get_top_keys",
 ]
 
 _lib = None
@@ -82,6 +82,8 @@ def lib():
         "mp_state_set_launch": ([vp, i32, i32], i32),
         "mp_state_get_launch": ([vp, P(i32), P(i32)], i32),
         "mp_state_set_work_hint": ([vp, vp], i32),
+        "mp_state_set_top_keys": ([vp, i32], i32),
+        "mp_state_get_top_keys": ([vp, P(i32)], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -325,6 +327,19 @@ def mp_state_get_launch(state: State):
     t, c = C.c_int(), C.c_int()
     _check(lib().mp_state_get_launch(state.handle, C.byref(t), C.byref(c)))
     return t.value, c.value
+
+
+def mp_state_set_top_keys(state: State, max_keys: int = 0):
+    """Cap the on-chip top level of a one-CTA-per-signal launch at max_keys
+    keys (a power of two; frames are grouped to fit); 0 restores the
+    default."""
+    _check(lib().mp_state_set_top_keys(state.handle, int(max_keys)))
+
+
+def mp_state_get_top_keys(state: State) -> int:
+    k = C.c_int()
+    _check(lib().mp_state_get_top_keys(state.handle, C.byref(k)))
+    return k.value
 
 
 def mp_state_set_work_hint(state: State, work=None):

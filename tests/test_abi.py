@@ -131,6 +131,11 @@ def test_null_handles_are_refused(libpath):
     assert lib.mp_state_set_work_hint(None, None) == mpgabor.MP_EINVAL
     assert b"null state" in lib.mp_last_error()
     assert lib.mp_state_set_launch(None, 128, 1) == mpgabor.MP_EINVAL
+    assert lib.mp_state_set_top_keys(None, 1024) == mpgabor.MP_EINVAL
+    assert b"null state" in lib.mp_last_error()
+    k = ctypes.c_int(-1)
+    assert lib.mp_state_get_top_keys(None, ctypes.byref(k)) == mpgabor.MP_EINVAL
+    assert k.value == -1
     assert lib.mp_state_set_resets(None, 1, 0.0) == mpgabor.MP_EINVAL
     assert lib.mp_get_status(None, None, None, None) == mpgabor.MP_EINVAL
     n = ctypes.c_int64()

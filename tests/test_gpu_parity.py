@@ -578,8 +578,8 @@ def test_graph_replay_and_autotune():
     st = mg.mp_analyze(plan, xd)
     mg.mp_run(st, 250, 200.0)
     direct = [mg.mp_get_atoms(st, b) for b in range(3)]
-    mg.mp_state_set_launch(st, *shape)
-    assert mg.mp_state_get_launch(st) == tuple(shape)
+    autotune.apply(st, shape)
+    assert mg.mp_state_get_launch(st) == tuple(shape[:2])
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
         mg.mp_analyze(plan, xd, st)
@@ -617,6 +617,43 @@ def test_work_hint_changes_order_not_results():
     with pytest.raises(mg.MPError):
         st = mg.mp_analyze(plan, xd)
         mg.mp_state_set_work_hint(st, [1.0, -1.0, 0.0, 0.0, 0.0, 0.0])
+
+
+def test_top_level_cap_changes_grouping_not_results():
+    """mp_state_set_top_keys: a smaller on-chip top level groups the frames
+    (896 frames of a 16384-sample signal into 224 or 56 keys) and changes no
+    decomposition; invalid caps, cluster launches and the reset by
+    mp_state_set_launch behave as declared."""
+    L, dicts = _workload_small("multi3")
+    xs = [inputs.as_f32(inputs.mixture(L, 80 + i, fs=16000.0)) for i in range(2)]
+    plan = _plan(dicts, 1e-4)
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    runs = []
+    for cap in (0, 256, 64):
+        st = mg.mp_analyze(plan, xd)
+        mg.mp_state_set_launch(st, 512, 1)
+        if cap:
+            mg.mp_state_set_top_keys(st, cap)
+        assert mg.mp_state_get_top_keys(st) == (cap or 16384)
+        mg.mp_run(st, 300, 200.0)
+        runs.append([(mg.mp_get_atoms(st, b), mg.mp_get_errors(st, b)) for b in range(2)])
+        st.close()
+    for r in runs[1:]:
+        for (a, e), (a0, e0) in zip(r, runs[0]):
+            assert np.array_equal(a, a0) and np.array_equal(e, e0)
+    st = mg.mp_analyze(plan, xd)
+    mg.mp_state_set_launch(st, 128, 1)
+    for bad in (100, 32, 8192):
+        with pytest.raises(mg.MPError) as ei:
+            mg.mp_state_set_top_keys(st, bad)
+        assert ei.value.code == mg.MP_EINVAL
+    mg.mp_state_set_top_keys(st, 512)
+    mg.mp_state_set_launch(st, 128, 1)
+    assert mg.mp_state_get_top_keys(st) == 4096
+    mg.mp_state_set_launch(st, 128, 4)
+    assert mg.mp_state_get_top_keys(st) == 0
+    with pytest.raises(mg.MPError):
+        mg.mp_state_set_top_keys(st, 1024)
 
 
 def test_bf16x3_resets_batched_only_flagged_signals_reanalysed():
