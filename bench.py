@@ -496,19 +496,29 @@ def run_batched(args, mg, torch, ws=1, rank=0):
     signals with the most atoms in the tuner's probe of this batch start
     first), analysis + MP captured in a CUDA graph and replayed.  The loop
     time with the default shape and order (longest signal first) is reported
-    beside it.  With several ranks the 256 signals are partitioned by length
-    over the ranks (no exchange; the totals are reduced)."""
+    beside it.  With several ranks the 256 signals are partitioned over the
+    ranks by their work: every rank decomposes the whole batch once (the
+    same deterministic atoms on every GPU, so every rank computes the same
+    partition without an exchange) and takes its share by atoms per signal;
+    the totals are reduced."""
     from paper_2202_12380_gb300 import autotune
 
     cfg, dicts, xs = _workload("batch256")
     n_all, L_all = len(xs), int(sum(len(x) for x in xs))
-    if ws > 1:
-        xs = [xs[i] for i in partition([len(x) for x in xs], ws)[rank]]
     stream = torch.cuda.Stream()
     aflag = mg.MP_ANALYSIS_BF16X3 if args.batched_analysis == "bf16x3" else mg.MP_ANALYSIS_FP32
     plan = mg.mp_plan_create([d[0] for d in dicts], [d[1] for d in dicts], [d[2] for d in dicts],
                              cfg["eps"], aflag, stream)
     xd = [torch.from_numpy(x).cuda() for x in xs]
+    split = "single"
+    if ws > 1:
+        probe = mg.mp_analyze(plan, xd)
+        mg.mp_run(probe, cfg["kmax"], cfg["snr_db"])
+        n_probe, _, _ = mg.mp_get_status(probe)
+        probe.close()
+        mine = partition([float(v) for v in n_probe], ws)[rank]
+        xs, xd = [xs[i] for i in mine], [xd[i] for i in mine]
+        split = "signals partitioned over %d ranks by atoms per signal" % ws
     # probe: the workload itself (its K and stop target), so the tail of the
     # long signals is part of what the tuner compares
     # the loop with the default launch order (longest signal first) and the
@@ -578,7 +588,7 @@ def run_batched(args, mg, torch, ws=1, rank=0):
            "cuda_graph": True, "atoms_per_step": int(atoms_all), "ms_per_step": t_max * 1e3,
            "analysis_ms": e[0].elapsed_time(e[1]), "mp_loop_ms": loop,
            "value": atoms_all / t_max, "unit": UNIT,
-           "parallelism": "signals partitioned over %d ranks" % ws if ws > 1 else "single",
+           "parallelism": split,
            "scaling": "strong" if ws > 1 else None,
            "analysis_roofline": analysis_roofline(plan, [len(x) for x in xs],
                                                   e[0].elapsed_time(e[1]))

@@ -10,19 +10,27 @@ update -- so a single-signal run on N GPUs is N replicas.
 from __future__ import annotations
 
 
-def partition(lengths, nranks: int):
-    """Length-balanced assignment of signals to ranks (longest first to the
-    least-loaded rank, ties to the lower rank).  Returns one ascending list
-    of signal indices per rank; deterministic for given inputs."""
+def partition(loads, nranks: int):
+    """Load-balanced assignment of signals to ranks: the largest load first
+    to the least-loaded rank, ties to the lower signal index and rank.  A
+    load is any non-negative per-signal cost: the signal length (the
+    default of the bench), or the atoms each signal needed in an earlier run
+    of similar signals, which is closer to its time (a pursuit that runs to
+    K_max costs more than a longer one that reaches its SNR early).  Returns
+    one ascending list of signal indices per rank; deterministic for given
+    inputs."""
     if nranks < 1:
         raise ValueError("nranks must be >= 1")
-    order = sorted(range(len(lengths)), key=lambda i: (-int(lengths[i]), i))
-    load = [0] * nranks
+    w = [float(x) for x in loads]
+    if any(not (x >= 0.0) or x == float("inf") for x in w):
+        raise ValueError("loads must be finite and >= 0")
+    order = sorted(range(len(w)), key=lambda i: (-w[i], i))
+    load = [0.0] * nranks
     out = [[] for _ in range(nranks)]
     for i in order:
         r = min(range(nranks), key=lambda q: (load[q], q))
         out[r].append(i)
-        load[r] += int(lengths[i])
+        load[r] += w[i]
     return [sorted(s) for s in out]
 
 

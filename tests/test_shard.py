@@ -25,6 +25,25 @@ def test_partition_covers_each_signal_once_and_balances():
         assert parts == partition(lens, n)  # deterministic
 
 
+def test_partition_by_work_balances_time_not_length():
+    """Loads other than lengths (e.g. atoms of an earlier run): the two
+    shortest signals run to K_max and carry the work.  By length they share
+    a rank (20 of the 22 units of work on one of three ranks); by work
+    each heavy signal gets a rank of its own."""
+    lens = [9, 8, 4, 3]
+    work = [1.0, 1.0, 10.0, 10.0]
+    by_len = partition(lens, 3)
+    assert by_len == [[0], [1], [2, 3]]
+    assert max(sum(work[i] for i in p) for p in by_len) == 20.0
+    by_work = partition(work, 3)
+    assert by_work == [[2], [3], [0, 1]]
+    assert max(sum(work[i] for i in p) for p in by_work) == 10.0
+    with pytest.raises(ValueError):
+        partition([1.0, -1.0], 2)
+    with pytest.raises(ValueError):
+        partition([float("nan")], 1)
+
+
 def test_partition_edge_cases():
     assert partition([], 2) == [[], []]
     assert partition([5], 3) == [[0], [], []]
