@@ -36,6 +36,13 @@ def test_library_exports_every_declared_symbol(libpath):
     assert not missing, missing
 
 
+def test_checked_library_exports_every_declared_symbol():
+    """The bounds-checking twin (-DMP_CHECK_BOUNDS) is the same ABI."""
+    lib = ctypes.CDLL(build.build(checked=True))
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
 def test_binding_covers_every_declared_symbol():
     assert sorted(mpgabor.EXPORTS) == declared_functions()
     for n in declared_functions():
